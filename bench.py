@@ -1,0 +1,456 @@
+#!/usr/bin/env python3
+"""Benchmark of the Minimod acoustic-isotropic step on GB300.
+
+Workload (one shot): 512^3 grid, 8-layer velocity model drawn from a seed,
+20-cell Cerjan sponge, 20 Hz Ricker source at a seeded cell, 64 receivers
+on the first plane below the top sponge, FP32, 1000 steps.  A benchmark
+"step" is one leapfrog step of the whole grid through the fused kernel
+(stencil, sponge, source, receivers, FP64 norm partials; every 25 steps the
+norm reduction).  The metric is Gpoint-updates per second.
+
+  value      device-resident: K timed steps of a shot whose model is already
+             in HBM, CUDA events on the launching stream, per-launch events
+             around every step kernel for the roofline.
+  e2e        the same metric through the C ABI with host buffers: domain
+             creation, velocity model from pinned host memory, source,
+             receivers, K steps (graph-replayed chunks) and the traces back
+             to pinned host memory, all inside the timed region.
+  roofline   the step kernel's algorithmic 16 B per point (read u_n, read
+             u_{n-1}, write u_{n+1}, read coef) per launch / its average
+             launch time, against the measured HBM copy bandwidth.
+  cpu_baseline  the FP64 oracle as it stands on the host cores, on a
+             bounded slab of the same workload.
+
+--impl reference times that oracle (the only reference implementation of
+this method; the paper ships no code) on the same workload, one bounded
+slab per step.  With N > 1 (torchrun) every rank runs an independent
+replica on its own GPU ("replicas only": the path has no data exchange
+between GPUs); value = all ranks' point-updates / the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 512
+ALG_BYTES_PER_POINT = 16          # FP32 3-level: u_n, u_{n-1}, coef in; u_{n+1} out
+METRIC = "stencil Gpts/s & % HBM roofline, FP32 vs BF16/FP16-store; shot p50/p99 latency"
+UNIT = "Gpts/s"
+KERNEL_SOURCES = ["paper_2506_02486_gb300/csrc/stencil.cuh",
+                  "paper_2506_02486_gb300/csrc/stencil_inst.cu",
+                  "paper_2506_02486_gb300/csrc/ptx.cuh",
+                  "paper_2506_02486_gb300/csrc/gw_device.h"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic() -> float | None:
+    """Per-launch DRAM bytes of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic_step_kernel.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    if rec.get("kernel_hash") != kernel_hash():
+        return None
+    return float(rec["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}",
+                 f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v: float) -> float:
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle
+
+def cpu_oracle_rate(shot, target_s: float, nthreads: int) -> tuple[float, str]:
+    """Oracle Gpts/s on a slab of the workload, sized to ~target_s."""
+    import oracle
+    oracle.build()
+    n = N_GRID
+    dt = oracle.time_step(shot.h, float(shot.vel.max()))
+    # calibrate on 8 planes
+    z0 = max(0, shot.src[2] - 4)
+    probe = shot.vel[z0:z0 + 8]
+    t = time.perf_counter()
+    oracle.run(probe, shot.h, 1, dt=dt, nthreads=nthreads)
+    per_pt = (time.perf_counter() - t) / probe.size
+    nz = int(max(8, min(n, target_s / 2 / (per_pt * n * n))))
+    z0 = max(0, min(n - nz, shot.src[2] - nz // 2))
+    slab = np.ascontiguousarray(shot.vel[z0:z0 + nz])
+    src = (shot.src[0], shot.src[1], shot.src[2] - z0)
+    steps = 2
+    t = time.perf_counter()
+    oracle.run(slab, shot.h, steps, dt=dt, src=src, f_peak=shot.f_peak,
+               sponge=shot.sponge, nthreads=nthreads)
+    el = time.perf_counter() - t
+    rate = slab.size * steps / el / 1e9
+    return rate, f"{n}x{n}x{nz} slab of the 512^3 layered model, {steps} steps, {el:.1f} s"
+
+
+def run_reference(args, world, rank, pg):
+    import workloads
+    if rank != 0:
+        return 0
+    shot = workloads.layered_cube(N_GRID)
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    dt = oracle.time_step(shot.h, float(shot.vel.max()))
+    n = N_GRID
+    # one bounded slab per step: pick its depth so the run takes minutes
+    probe = np.ascontiguousarray(shot.vel[:8])
+    t = time.perf_counter()
+    oracle.run(probe, shot.h, 1, dt=dt, nthreads=cores)
+    per_pt = (time.perf_counter() - t) / probe.size
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    nz = int(max(8, min(n, budget / (per_pt * n * n))))
+    z0 = max(0, min(n - nz, shot.src[2] - nz // 2))
+    slab = np.ascontiguousarray(shot.vel[z0:z0 + nz])
+    src = (shot.src[0], shot.src[1], shot.src[2] - z0)
+    state = None
+
+    def one(state):
+        u0, um1 = (None, None) if state is None else state
+        r = oracle.run(slab, shot.h, 1, dt=dt, src=src, f_peak=shot.f_peak,
+                       sponge=shot.sponge, u0=u0, um1=um1, nthreads=cores)
+        return r["u"], r["u_prev"]
+
+    for _ in range(args.warmup):
+        state = one(state)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        state = one(state)
+    el = time.perf_counter() - t
+    value = slab.size * args.steps / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / max(1, args.steps) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "layered_512cubed (per step: one slab)",
+                   "slab": [n, n, nz], "sponge": shot.sponge},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{n}x{n}x{nz} slab of the 512^3 layered "
+                                   f"model per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ ours
+
+def seg_bytes(nx, ny, nz, dtype, px=1, py=1, pz=1):
+    from paper_2506_02486_gb300.runtime import padded_bytes
+    nsub = px * py * pz
+    sub = padded_bytes(-(-nx // px), -(-ny // py), -(-nz // pz), dtype)
+    return nsub * (4 * sub + (320 << 20))
+
+
+def run_shot_device(seg, shot, steps, warmup, dtype="f32", px=1, py=1, pz=1,
+                    timing=True, stream=None, sampler=None):
+    """Device-resident timing; returns (elapsed_ms, kernel_stats, info)."""
+    import torch
+    from paper_2506_02486_gb300 import gbwave as gw
+    from paper_2506_02486_gb300.runtime import Shot
+    n = N_GRID
+    with Shot(seg, n, n, n, px=px, py=py, pz=pz, nsteps=steps + warmup,
+              dtype=dtype, sponge=shot.sponge) as s:
+        s.set_model(shot.vel)
+        s.add_ricker(shot.src, shot.f_peak)
+        s.set_receivers(shot.receivers)
+        st = stream or torch.cuda.current_stream()
+        s.step(warmup, st)
+        gw.gw_barrier(s.dom, st, True)
+        gw.gw_kernel_timing(s.dom, timing)
+        if timing:
+            gw.gw_kernel_stats_get(s.dom)        # reset
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        e0.record(st)
+        s.step(steps, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        ms = e0.elapsed_time(e1)
+        stats = gw.gw_kernel_stats_get(s.dom) if timing else None
+        gw.gw_kernel_timing(s.dom, False)
+        info = s.info
+        norms = s.norms(min(steps + warmup, 50))
+    return ms, stats, info, clocks, norms
+
+
+def run_e2e(seg, shot, steps):
+    """The user's call sequence with host buffers, timed end to end."""
+    import torch
+    from paper_2506_02486_gb300 import gbwave as gw
+    n = N_GRID
+    vel_pinned = torch.empty(shot.vel.shape, dtype=torch.float64,
+                             pin_memory=True)
+    vel_pinned.numpy()[...] = shot.vel
+    traces = torch.empty((shot.receivers.shape[0], steps), dtype=torch.float32,
+                         pin_memory=True)
+    rec = np.ascontiguousarray(shot.receivers, dtype=np.int32)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    desc = gw.shot_desc(n, n, n, nsteps=steps, sponge=shot.sponge)
+    dom = gw.gw_domain_create(seg.ctx, desc)
+    try:
+        gw.gw_set_model(dom, vel_pinned.numpy())
+        dt = gw.gw_domain_info_get(dom)["dt"]
+        wl = gw.gw_ricker(shot.f_peak, dt, steps)
+        gw.gw_inject_source(dom, *shot.src, wl)
+        gw.gw_set_receivers(dom, rec)
+        gw.gw_step(dom, steps, torch.cuda.current_stream())
+        gw.gw_read_receivers(dom, rec.shape[0], steps, out=traces.numpy())
+    finally:
+        gw.gw_domain_destroy(dom)
+    el = time.perf_counter() - t
+    h2d = shot.vel.nbytes + wl.nbytes + rec.nbytes
+    d2h = traces.numel() * 4
+    return el, h2d, d2h
+
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+    import workloads
+    from paper_2506_02486_gb300 import buildlib
+    from paper_2506_02486_gb300.runtime import Segment
+
+    buildlib.build()
+    torch.cuda.set_device(local)
+    shot = workloads.layered_cube(N_GRID)
+    n = N_GRID
+    npts = n ** 3
+    seg = Segment(seg_bytes(n, n, n, "f32", 2, 2, 2), nranks=8, device=local)
+    seg1 = Segment(seg_bytes(n, n, n, "f32"), nranks=1, device=local)
+    try:
+        sampler = ClockSampler(local) if rank == 0 else None
+        barrier(pg)
+        ms, stats, info, clocks, norms = run_shot_device(
+            seg1, shot, args.steps, args.warmup, sampler=sampler)
+        ms_max = max_over_ranks(pg, ms)
+        value = world * npts * args.steps / (ms_max * 1e-3) / 1e9
+        # e2e through the public API with host buffers
+        barrier(pg)
+        e2e_s, h2d, d2h = run_e2e(seg1, shot, args.steps)
+        e2e_s = max_over_ranks(pg, e2e_s)
+        e2e_value = world * npts * args.steps / e2e_s / 1e9
+        variants = {}
+        if args.variants:
+            vs = max(100, args.steps // 5)
+            for name, kw in (("f32_2x2x2_fused_halo", dict(px=2, py=2, pz=2)),
+                             ("f16s_delta", dict(dtype="f16s")),
+                             ("bf16_delta", dict(dtype="bf16"))):
+                segv = seg if name.startswith("f32_2x2x2") else seg1
+                vms, vstats, _, _, _ = run_shot_device(
+                    segv, shot, vs, args.warmup, **kw)
+                kavg = vstats["total_ms"] / max(1, vstats["launches"])
+                variants[name] = {
+                    "gpts": npts * vs / (vms * 1e-3) / 1e9,
+                    "kernel_ms": kavg,
+                    "steps": vs,
+                }
+    finally:
+        seg.close()
+        seg1.close()
+    if rank != 0:
+        return 0
+    peak, peak_kind = measured_peak()
+    kavg_ms = stats["total_ms"] / max(1, stats["launches"])
+    achieved = ALG_BYTES_PER_POINT * npts / (kavg_ms * 1e-3) / 1e9
+    traffic = recorded_traffic()
+    cpu_rate, cpu_sample = (None, None)
+    cores = os.cpu_count() or 1
+    if args.cpu_baseline:
+        cpu_rate, cpu_sample = cpu_oracle_rate(shot, 20.0, cores)
+    gpu_launches = stats["launches"] + -(-args.steps // 25)   # + norm reductions
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": "layered_512cubed", "grid": [n, n, n],
+            "sponge": shot.sponge, "source_hz": shot.f_peak,
+            "receivers": int(shot.receivers.shape[0]),
+            "decomposition": "1x1x1", "halo": "fused",
+            "parallelism": f"replicas{world}",
+            "tile": info["tile"], "ctas": info["ctas"], "items": info["items"],
+            "l2": "inputs larger than L2: 3 fields x 588 MB streamed per step",
+            "timing": "CUDA events on the launching stream, per-launch events",
+        },
+        "roofline": {
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_kind": peak_kind,
+            "alg_bytes_per_launch": ALG_BYTES_PER_POINT * npts,
+            "kernel_ms": kavg_ms,
+        },
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / args.steps,
+                "d2h_bytes_per_step": d2h / args.steps,
+                "scope": "domain create + set_model (pinned FP64) + source + "
+                         "receivers + K graph-chunked steps + traces D2H"},
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+        "variants": variants,
+        "kernel_hash": kernel_hash(),
+    }
+    if cpu_rate is not None:
+        line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT,
+                                "cores": cores, "kind": "oracle",
+                                "sample": cpu_sample}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=25)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-variants", dest="variants", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline",
+                    action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        # the oracle runs on rank 0's host cores only; no GPU, no collective
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        return run_reference(args, world, rank, None)
+    world, rank, local, pg = dist_setup()
+    try:
+        return run_ours(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

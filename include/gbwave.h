@@ -1,0 +1,290 @@
+/*
+ * gbwave.h -- C ABI of the GB300 (sm_103a) Minimod acoustic-isotropic
+ * library: PGAS-style global memory, subdomain halo put / fence, and the
+ * fused 25-point-stencil leapfrog time step.
+ *
+ * Paper: "DiOMP-Offloading: Toward Portable Distributed Heterogeneous
+ * OpenMP" (arXiv 2506.02486).  Section 3.2 defines the global segment with
+ * symmetric and asymmetric allocation (32-byte second-level pointers and a
+ * remote-pointer cache); Listing 1 (section 4.5) is the Minimod halo
+ * exchange: every rank puts its boundary slabs into its neighbours with a
+ * one-sided device-to-device put, then fences.  Here the "ranks" are the
+ * subdomains of one grid, all resident in one GPU's HBM, and a put is a
+ * device store into the neighbour's halo.
+ *
+ * The numerical scheme (not printed in the paper, which names only the
+ * "acoustic isotropic kernel" of Minimod, section 4.5):
+ *
+ *   lap(u)  = sum over x, y, z of c0 u + sum_{m=1..4} c_m (u[-m] + u[+m]),
+ *             c = (-205/72, 8/5, -1/5, 8/315, -1/560)
+ *   u_{n+1} = G (2 u_n - G u_{n-1} + coef (lap(u_n) + src_n)),
+ *   coef    = (v dt / h)^2,   G = g_x g_y g_z (Cerjan sponge),
+ *   src_n   = wavelet[n] at the source cell(s), 0 elsewhere.
+ *
+ * Conventions for every entry point:
+ *   - Return value: GW_OK (0) or a negative GW_ERR_* code; nothing aborts.
+ *     gw_last_error() gives a message for the calling thread.
+ *   - Device work is enqueued on the gw_stream argument (a cudaStream_t;
+ *     NULL = the legacy default stream) and is asynchronous unless the
+ *     entry point says it synchronises.  Faults found by kernels (a wait
+ *     that gave up, a non-finite norm) are latched in a device error word
+ *     and reported by the next synchronising call.
+ *   - Host arrays are owned by the caller and only read/written during the
+ *     call.  Interior host arrays are x fastest, then y, then z
+ *     (index (z*ny + y)*nx + x), with no halo.
+ *   - The global segment is device memory owned by the caller (e.g. a
+ *     PyTorch tensor); the library sub-allocates it and owns only its
+ *     own metadata.  Destroy domains before releasing the segment.
+ */
+#ifndef GBWAVE_H
+#define GBWAVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int gw_status;
+#define GW_OK            0
+#define GW_ERR_ARG      -1   /* invalid argument                          */
+#define GW_ERR_BUDGET   -2   /* does not fit the segment / HBM budget     */
+#define GW_ERR_ALIGN    -3   /* pointer or size misaligned                */
+#define GW_ERR_CUDA     -4   /* a CUDA runtime call failed                */
+#define GW_ERR_TIMEOUT  -5   /* a bounded device or host wait gave up     */
+#define GW_ERR_STATE    -6   /* call not valid in the object's state      */
+#define GW_ERR_NUMERIC  -7   /* a check reduction found a non-finite value */
+#define GW_ERR_NOMEM    -8   /* host allocation failed                    */
+
+typedef struct gw_ctx gw_ctx;
+typedef struct gw_domain gw_domain;
+typedef struct gw_batch gw_batch;
+typedef struct gw_server gw_server;
+typedef void *gw_stream;          /* cudaStream_t */
+typedef uint64_t gw_gptr;         /* handle of a global allocation; 0 = none */
+
+/* Storage types of the wavefields.  Arithmetic is FP32 for GW_F32,
+ * GW_F16S and GW_BF16, FP64 for GW_F64.  GW_F16S stores FP16 scaled by a
+ * per-shot power of two; the reduced types use the delta form
+ * w_n = u_n - G u_{n-1}:  w' = G (w + coef (lap(u) + src)),  u' = G u + w'
+ * (algebraically the same recurrence; see the library's design notes). */
+enum { GW_F32 = 0, GW_F64 = 1, GW_F16S = 2, GW_BF16 = 3 };
+
+/* How the halo of each subdomain is refreshed after a step. */
+enum {
+    GW_HALO_FUSED = 0,     /* the step kernel stores boundary values straight
+                              into the neighbours' halos (one-sided put in
+                              the epilogue); fence = kernel boundary      */
+    GW_HALO_SEPARATE = 1   /* a pack/put/unpack kernel after each step    */
+};
+
+/* Fields readable/writable through gw_read_wavefield / gw_write_wavefield. */
+enum {
+    GW_FIELD_U = 0,        /* u_n, the current wavefield                  */
+    GW_FIELD_UPREV = 1,    /* u_{n-1} (3-level storage only)              */
+    GW_FIELD_W = 2,        /* w_n = u_n - G u_{n-1} (delta storage only)  */
+    GW_FIELD_COEF = 3      /* (v dt / h)^2 as stored                       */
+};
+
+/* One shot (one grid).  Zero-initialise and set what you need. */
+typedef struct {
+    int nx, ny, nz;        /* interior grid points                        */
+    double h;              /* grid spacing (m)                            */
+    double courant;        /* nu = vmax dt / h; <= 0: half the stability
+                              limit, nu = 0.5 * sqrt(4 / (3 |L(pi)|))     */
+    double dt;             /* > 0: use this time step, ignore courant     */
+    int nsteps;            /* capacity of the wavelet / trace / norm logs */
+    int dtype;             /* GW_F32, GW_F64, GW_F16S, GW_BF16            */
+    int sponge;            /* Cerjan layer width in cells (0 = none)      */
+    double sponge_a;       /* Cerjan constant; <= 0: 0.015                */
+    int periodic;          /* bit 0: x, bit 1: y, bit 2: z wrap around    */
+    int halo_mode;         /* GW_HALO_FUSED or GW_HALO_SEPARATE           */
+    int chunk;             /* steps per CUDA-graph chunk; 0: 25; < 0: no
+                              graphs (plain launches)                     */
+    int tile;              /* kernel tile configuration id + 1; 0: default */
+    int zchunk;            /* planes per work item; 0: chosen by the cost
+                              model (load balance vs z-halo re-reads)     */
+    double scale_u;        /* GW_F16S: power-of-two scale of u; 0: auto   */
+    double scale_w;        /* GW_F16S: power-of-two scale of w; 0: auto   */
+} gw_shot_desc;
+
+typedef struct {
+    double dt;             /* time step used (s)                          */
+    double courant;        /* vmax dt / h                                 */
+    double vmax;           /* max velocity of the model (0 before set)    */
+    int nsub;              /* number of subdomains                        */
+    int step;              /* steps taken                                 */
+    int tile;              /* kernel tile configuration in use            */
+    int ctas;              /* CTAs per step launch                        */
+    int items;             /* work items (tile columns x z-chunks)        */
+    double scale_u, scale_w;
+    size_t device_bytes;   /* segment bytes held by the domain            */
+} gw_domain_info;
+
+typedef struct {
+    int launches;          /* step-kernel launches timed                  */
+    double total_ms;       /* summed device time of those launches        */
+    double halo_ms;        /* summed device time of separate halo kernels */
+} gw_kernel_stats;
+
+/* ------------------------------------------------------------------ */
+/* errors and context                                                  */
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *gw_last_error(void);
+/* Short name of a status code. */
+const char *gw_status_string(gw_status s);
+/* Library version string. */
+const char *gw_version(void);
+
+/* Create a context on CUDA device `device` (>= 0).  device = -1 creates a
+ * host-only context whose "segment" is host memory: allocation, address
+ * translation and the pointer cache work, nothing runs on a GPU (used to
+ * test the allocator without a GPU). */
+gw_status gw_ctx_create(gw_ctx **out, int device);
+gw_status gw_ctx_destroy(gw_ctx *ctx);
+
+/* ------------------------------------------------------------------ */
+/* global segment and PGAS allocation (paper section 3.2)              */
+
+/* Attach the caller's buffer [base, base + bytes) as the global segment,
+ * divided into `nranks` equal per-rank segments (bytes / nranks rounded
+ * down to 4 KiB).  base must be 256-byte aligned.  Symmetric allocations
+ * grow upward from each rank segment's base at the same offset on every
+ * rank; asymmetric data grows downward from each rank segment's end, as in
+ * the paper's Figure "memory".  The buffer is zeroed on attach when
+ * zero != 0 (device contexts only). */
+gw_status gw_segment_attach(gw_ctx *ctx, void *base, size_t bytes,
+                            int nranks, int zero);
+/* Per-rank bytes, bytes used by symmetric and (max over ranks) asymmetric
+ * allocations. */
+gw_status gw_segment_info(gw_ctx *ctx, size_t *rank_bytes, size_t *sym_used,
+                          size_t *asym_used);
+
+/* Symmetric allocation (section 3.2): every rank gets `bytes` at the same
+ * offset, so rank r's block is segment_base(r) + offset.  256-byte aligned.
+ * GW_ERR_BUDGET if it does not fit. */
+gw_status gw_alloc_symmetric(gw_ctx *ctx, size_t bytes, gw_gptr *out);
+/* Asymmetric allocation (section 3.2): rank r gets bytes[r] (nranks
+ * entries, zero allowed).  A 32-byte second-level pointer record is
+ * allocated symmetrically; rank r's data is placed at the end of its
+ * segment and its record is set to point to it.  Record layout (device
+ * memory, little-endian): u64 address, u64 bytes, u32 rank, u32 flags,
+ * u64 reserved. */
+gw_status gw_alloc_asymmetric(gw_ctx *ctx, const size_t *bytes,
+                              gw_gptr *out);
+/* Free an allocation on every rank; cached translations of it are dropped. */
+gw_status gw_free(gw_ctx *ctx, gw_gptr g);
+/* Translate (g, rank) to an address in rank's segment.  Symmetric: base of
+ * rank + offset.  Asymmetric: the second-level record of that rank is read
+ * (one device-to-host fetch) the first time and served from the remote
+ * pointer cache afterwards.  bytes (may be NULL) receives the size. */
+gw_status gw_resolve(gw_ctx *ctx, gw_gptr g, int rank, void **addr,
+                     size_t *bytes);
+/* Hits and misses of the remote pointer cache. */
+gw_status gw_ptr_cache_stats(gw_ctx *ctx, uint64_t *hits, uint64_t *misses);
+
+/* One-sided put (section 3.2, Listing 1's ompx_put with D2D): copy `bytes`
+ * from device address src into rank dst_rank's block of g at byte offset
+ * dst_off, on `stream`.  GW_ERR_ARG if out of the block. */
+gw_status gw_put(gw_ctx *ctx, gw_gptr dst, int dst_rank, size_t dst_off,
+                 const void *src, size_t bytes, gw_stream stream);
+/* One-sided get: the mirror of gw_put. */
+gw_status gw_get(gw_ctx *ctx, void *dst, gw_gptr src, int src_rank,
+                 size_t src_off, size_t bytes, gw_stream stream);
+/* Fence (Listing 1's ompx_fence): every put/get issued through this
+ * context on any stream is complete and visible to work enqueued on
+ * `stream` afterwards (stream order; no host synchronisation). */
+gw_status gw_fence(gw_ctx *ctx, gw_stream stream);
+
+/* ------------------------------------------------------------------ */
+/* domains: one shot, decomposed into px*py*pz subdomains              */
+
+/* Create a shot domain decomposed into px x py x pz subdomains (subdomain
+ * (i, j, k) is rank (k*py + j)*px + i; the segment needs at least that
+ * many ranks).  split_x/y/z (px/py/pz entries, may be NULL for an even
+ * split, larger pieces first) give the interior extent of each slab.
+ * symmetric != 0: every subdomain array is padded to the largest
+ * subdomain and allocated symmetrically (offset translation); symmetric = 0:
+ * exact sizes, asymmetric allocation through second-level pointers.
+ * Allocates its fields from the segment; wavefields start at zero. */
+gw_status gw_domain_create(gw_ctx *ctx, const gw_shot_desc *desc, int px,
+                           int py, int pz, const int *split_x,
+                           const int *split_y, const int *split_z,
+                           int symmetric, gw_domain **out);
+gw_status gw_domain_destroy(gw_domain *d);
+gw_status gw_domain_info_get(gw_domain *d, gw_domain_info *out);
+
+/* Velocity model (m/s), nx*ny*nz FP64 host values.  Computes vmax on the
+ * GPU, then dt (from desc.dt or desc.courant) and coef = (v dt / h)^2 in
+ * FP64 on the GPU, rounded to the storage type.  Synchronises. */
+gw_status gw_set_model(gw_domain *d, const double *vel_host);
+/* The same from FP32 host values. */
+gw_status gw_set_model_f32(gw_domain *d, const float *vel_host);
+
+/* Ricker wavelet r(t_n) = (1 - 2 a) exp(-a), a = (pi f (n dt - 1/f))^2,
+ * computed in FP64 and rounded to FP32.  Pure host function. */
+gw_status gw_ricker(double f_peak, double dt, int n, float *out);
+
+/* Add a point source at global interior cell (gx, gy, gz) with wavelet
+ * samples wavelet[0..n) (FP32 host; sample n is added to lap(u_n) when
+ * computing u_{n+1}; steps beyond n add nothing).  Up to 16 sources. */
+gw_status gw_inject_source(gw_domain *d, int gx, int gy, int gz,
+                           const float *wavelet, int n);
+/* Receivers: nrec (x, y, z) global interior cells; trace sample n is
+ * u_{n+1} at the receiver, for n < desc.nsteps.  Replaces earlier ones. */
+gw_status gw_set_receivers(gw_domain *d, int nrec, const int *xyz);
+
+/* Advance nsteps steps on `stream`: K-step chunks (desc.chunk) replayed
+ * from an instantiated CUDA graph, the remainder launched directly.  Each
+ * step is one launch of the fused kernel over all subdomains (stencil,
+ * sponge, source, receivers, norm partials and, in GW_HALO_FUSED mode, the
+ * halo puts), plus the put kernel in GW_HALO_SEPARATE mode; each chunk
+ * ends with the FP64 norm reduction.  Asynchronous. */
+gw_status gw_step(gw_domain *d, int nsteps, gw_stream stream);
+/* Refresh every subdomain's face halos of the current wavefield u_n from
+ * its neighbours (pack/put/unpack kernel; Listing 1's puts). */
+gw_status gw_put_halo(gw_domain *d, gw_stream stream);
+/* Fence (Listing 1's ompx_fence): all puts enqueued so far are complete
+ * and visible to later work on `stream`.  With sync != 0 also waits on the
+ * host and reports latched device errors. */
+gw_status gw_barrier(gw_domain *d, gw_stream stream, int sync);
+
+/* Copy traces to host: out[r*nsteps + n], FP32, for r < nrec, n < nsteps
+ * (<= desc.nsteps).  Synchronises the domain's work. */
+gw_status gw_read_receivers(gw_domain *d, float *host_out, int nrec,
+                            int nsteps);
+/* Gather a field into an interior host array (FP64 if f64 != 0, else
+ * FP32), unscaled.  Synchronises. */
+gw_status gw_read_wavefield(gw_domain *d, int which, void *host_out,
+                            int f64);
+/* Scatter an interior host array (FP64 if f64 != 0, else FP32) into a
+ * field, rounding to the storage type, then refresh its halos.
+ * Synchronises. */
+gw_status gw_write_wavefield(gw_domain *d, int which, const void *host_in,
+                             int f64);
+/* Per-step sum of u_{n+1}^2 (FP64 sum of FP32 partials) for steps
+ * [0, n); n <= steps taken and <= desc.nsteps.  Synchronises. */
+gw_status gw_norms(gw_domain *d, double *host_out, int n);
+/* FP64 check reductions of the current state: norm2 = sum u_n^2 and
+ * energy = sum (u_n - u_{n-1})^2 / coef - sum u_n lap(u_{n-1})
+ * (conserved without source and sponge).  Either pointer may be NULL.
+ * Synchronises; GW_ERR_NUMERIC if non-finite. */
+gw_status gw_check(gw_domain *d, double *norm2, double *energy);
+
+/* Record the device time of every step-kernel launch (CUDA events) while
+ * enabled; gw_kernel_stats_get returns the totals and resets them. */
+gw_status gw_kernel_timing(gw_domain *d, int enable);
+gw_status gw_kernel_stats_get(gw_domain *d, gw_kernel_stats *out);
+
+/* Raw storage copy of the whole state (both wavefields, step counter) for
+ * checkpoint/restart; gw_state_bytes gives the size.  Synchronises. */
+gw_status gw_state_bytes(gw_domain *d, size_t *bytes);
+gw_status gw_save_state(gw_domain *d, void *host_out);
+gw_status gw_load_state(gw_domain *d, const void *host_in);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBWAVE_H */

@@ -1,0 +1,339 @@
+// aux_kernels.cu -- the kernels around the fused step: model precompute
+// (vmax, coef = (v dt / h)^2 in FP64), dense <-> padded field transfers,
+// the separate face-halo put (pack/put/unpack of Listing 1, section 4.5),
+// the end-of-chunk FP64 norm reduction, and the FP64 energy check.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "gw_device.h"
+#include "gw_kernels.h"
+
+namespace gw {
+
+// ---------------------------------------------------------------- scalars
+
+template <class T> __device__ __forceinline__ double to_d(T v);
+template <> __device__ __forceinline__ double to_d<float>(float v) { return v; }
+template <> __device__ __forceinline__ double to_d<double>(double v) { return v; }
+template <> __device__ __forceinline__ double to_d<__half>(__half v) { return (double)__half2float(v); }
+template <> __device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+template <class T> __device__ __forceinline__ T from_d(double v);
+template <> __device__ __forceinline__ float from_d<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ double from_d<double>(double v) { return v; }
+template <> __device__ __forceinline__ __half from_d<__half>(double v) { return __double2half(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+
+__device__ __forceinline__ size_t pidx(const SubDev &s, int xo, int x, int y, int z)
+{
+    return ((size_t)(z + R) * s.py + (size_t)(y + R)) * s.px + (size_t)(xo + x);
+}
+
+// ---------------------------------------------------------------- vmax
+
+template <class V>
+__global__ void k_vmax(const V *v, size_t n, unsigned long long *out)
+{
+    double m = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        double x = (double)v[i];
+        m = x > m ? x : m;     // a NaN never wins
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        double t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+    }
+    // non-negative doubles order like their bit patterns
+    if ((threadIdx.x & 31) == 0 && m > 0.0)
+        atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+cudaError_t launch_vmax(const void *v, size_t n, int f32,
+                        unsigned long long *out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    int grid = (int)((n + 255) / 256);
+    grid = grid > 4096 ? 4096 : grid;
+    if (f32)
+        k_vmax<float><<<grid, 256, 0, s>>>(static_cast<const float *>(v), n, out);
+    else
+        k_vmax<double><<<grid, 256, 0, s>>>(static_cast<const double *>(v), n, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- coef
+
+template <class CT, class V>
+__global__ void k_coef(ModelSlab m, SubDev sd, int xo)
+{
+    // planes of the slab inside this subdomain
+    int zl = max(m.z_lo, sd.gz0), zh = min(m.z_hi, sd.gz0 + sd.nz);
+    if (zl >= zh) return;
+    size_t npl = (size_t)sd.nx * sd.ny;
+    size_t n = npl * (size_t)(zh - zl);
+    const V *v = static_cast<const V *>(m.v);
+    CT *c = reinterpret_cast<CT *>(sd.coef);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % sd.nx);
+        int y = (int)((i / sd.nx) % sd.ny);
+        int gz = zl + (int)(i / npl);
+        size_t src = ((size_t)(gz - m.z_lo) * m.NY + (size_t)(sd.gy0 + y)) * m.NX +
+                     (size_t)(sd.gx0 + x);
+        double nu = (double)v[src] * m.dt_over_h;   // FP64 precompute
+        c[pidx(sd, xo, x, y, gz - sd.gz0)] = from_d<CT>(nu * nu);
+    }
+}
+
+static int grid_for(size_t n)
+{
+    size_t g = (n + 255) / 256;
+    return (int)(g > 8192 ? 8192 : (g ? g : 1));
+}
+
+cudaError_t launch_coef(const ModelSlab &m, const SubDev &sd, int dtype,
+                        cudaStream_t s)
+{
+    size_t n = (size_t)sd.nx * sd.ny * (size_t)(m.z_hi - m.z_lo);
+    int g = grid_for(n);
+    int xo = dtype_xoff(dtype);
+#define GW_COEF(CT)                                                     \
+    (m.f32 ? (k_coef<CT, float><<<g, 256, 0, s>>>(m, sd, xo), 0)        \
+           : (k_coef<CT, double><<<g, 256, 0, s>>>(m, sd, xo), 0))
+    switch (dtype) {
+    case DT_F32: GW_COEF(float); break;
+    case DT_F64: GW_COEF(double); break;
+    default: GW_COEF(__half); break;   // reduced storage keeps coef in FP16
+    }
+#undef GW_COEF
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- transfers
+
+template <class T, class D, bool SCATTER>
+__global__ void k_xfer(FieldSlab f, SubDev sd, int xo)
+{
+    int zl = max(f.z_lo, sd.gz0), zh = min(f.z_hi, sd.gz0 + sd.nz);
+    if (zl >= zh) return;
+    size_t npl = (size_t)sd.nx * sd.ny;
+    size_t n = npl * (size_t)(zh - zl);
+    char *base = f.which == 0 ? sd.u[f.cur] : f.which == 1 ? sd.u[f.cur ^ 1]
+               : f.which == 2 ? sd.w : sd.coef;
+    T *a = reinterpret_cast<T *>(base);
+    D *d = static_cast<D *>(f.dense);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % sd.nx);
+        int y = (int)((i / sd.nx) % sd.ny);
+        int gz = zl + (int)(i / npl);
+        size_t di = ((size_t)(gz - f.z_lo) * f.NY + (size_t)(sd.gy0 + y)) * f.NX +
+                    (size_t)(sd.gx0 + x);
+        size_t pi = pidx(sd, xo, x, y, gz - sd.gz0);
+        if (SCATTER)
+            a[pi] = from_d<T>((double)d[di] * f.scale);
+        else
+            d[di] = (D)(to_d<T>(a[pi]) / f.scale);
+    }
+}
+
+template <bool SCATTER>
+static cudaError_t xfer(const FieldSlab &f, const SubDev &sd, int dtype,
+                        cudaStream_t s)
+{
+    size_t n = (size_t)sd.nx * sd.ny * (size_t)(f.z_hi - f.z_lo);
+    int g = grid_for(n);
+    int xo = dtype_xoff(dtype);
+    bool coef = f.which == 3;
+#define GW_X(T)                                                              \
+    (f.f64 ? (k_xfer<T, double, SCATTER><<<g, 256, 0, s>>>(f, sd, xo), 0)    \
+           : (k_xfer<T, float, SCATTER><<<g, 256, 0, s>>>(f, sd, xo), 0))
+    switch (dtype) {
+    case DT_F32: GW_X(float); break;
+    case DT_F64: GW_X(double); break;
+    case DT_F16S: if (coef) GW_X(__half); else GW_X(__half); break;
+    case DT_BF16: if (coef) GW_X(__half); else GW_X(__nv_bfloat16); break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef GW_X
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const FieldSlab &f, const SubDev &sd, int dtype,
+                           cudaStream_t s)
+{
+    return xfer<true>(f, sd, dtype, s);
+}
+
+cudaError_t launch_gather(const FieldSlab &f, const SubDev &sd, int dtype,
+                          cudaStream_t s)
+{
+    return xfer<false>(f, sd, dtype, s);
+}
+
+// ---------------------------------------------------------------- halo put
+
+// Element counts and the source/destination boxes of one face copy.
+__device__ __forceinline__ void face_box(const SubDev &s, const SubDev &d,
+                                         int face, int &ex, int &ey, int &ez,
+                                         int &sx, int &sy, int &sz, int &dx,
+                                         int &dy, int &dz)
+{
+    ex = s.nx; ey = s.ny; ez = s.nz;
+    sx = sy = sz = 0;
+    dx = dy = dz = 0;
+    switch (face) {
+    case 0: ex = R; sx = 0;        dx = d.nx; break;   // -x slab -> nbr's +x halo
+    case 1: ex = R; sx = s.nx - R; dx = -R;   break;   // +x slab -> nbr's -x halo
+    case 2: ey = R; sy = 0;        dy = d.ny; break;
+    case 3: ey = R; sy = s.ny - R; dy = -R;   break;
+    case 4: ez = R; sz = 0;        dz = d.nz; break;
+    default: ez = R; sz = s.nz - R; dz = -R;  break;
+    }
+}
+
+template <class E>
+__global__ void k_halo(const HaloDesc *descs, int ndesc, long long total,
+                       const SubDev *subs, const int *step, int k, int xo)
+{
+    int buf = (*step + k + 1) & 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+         i < total; i += (long long)gridDim.x * blockDim.x) {
+        int di = 0;
+        while (di + 1 < ndesc && descs[di + 1].first <= i) ++di;
+        const HaloDesc hd = descs[di];
+        const SubDev &s = subs[hd.src];
+        const SubDev &d = subs[hd.dst];
+        int ex, ey, ez, sx, sy, sz, dx, dy, dz;
+        face_box(s, d, hd.face, ex, ey, ez, sx, sy, sz, dx, dy, dz);
+        long long j = i - hd.first;
+        int a = (int)(j % ex);
+        int b = (int)((j / ex) % ey);
+        int c = (int)(j / ((long long)ex * ey));
+        // the halo cell of d keeps d's own x/y/z for the axes not crossed
+        const E *src = reinterpret_cast<const E *>(s.u[buf]);
+        E *dst = reinterpret_cast<E *>(d.u[buf]);
+        int fx = hd.face >> 1;
+        int tx = fx == 0 ? dx + a : a;
+        int ty = fx == 1 ? dy + b : b;
+        int tz = fx == 2 ? dz + c : c;
+        dst[pidx(d, xo, tx, ty, tz)] = src[pidx(s, xo, sx + a, sy + b, sz + c)];
+    }
+}
+
+cudaError_t launch_halo(const HaloDesc *descs, int ndesc, long long total,
+                        const SubDev *subs_dev, const int *step, int k,
+                        int dtype, cudaStream_t s)
+{
+    if (total <= 0 || ndesc <= 0) return cudaSuccess;
+    int g = grid_for((size_t)total);
+    int xo = dtype_xoff(dtype);
+    switch (dtype_size(dtype)) {
+    case 2: k_halo<unsigned short><<<g, 256, 0, s>>>(descs, ndesc, total, subs_dev, step, k, xo); break;
+    case 4: k_halo<unsigned int><<<g, 256, 0, s>>>(descs, ndesc, total, subs_dev, step, k, xo); break;
+    default: k_halo<unsigned long long><<<g, 256, 0, s>>>(descs, ndesc, total, subs_dev, step, k, xo); break;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- chunk end
+
+__global__ void k_chunk_end(const ShotDev *shots, const double *partials,
+                            int nitems, int nk, unsigned *err)
+{
+    const ShotDev &sh = shots[blockIdx.x];
+    __shared__ double red[256];
+    const int n0 = *sh.step;
+    for (int k = 0; k < nk; ++k) {
+        const double *p = partials + (size_t)k * nitems + sh.first_item;
+        double v = 0.0;
+        for (int i = threadIdx.x; i < sh.nitems; i += blockDim.x) v += p[i];
+        red[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            double s = red[0];
+            if (n0 + k < sh.cap) sh.norms[n0 + k] = s;
+            if (!isfinite(s)) atomicOr(err, ERRB_NONFINITE);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *sh.step = n0 + nk;
+}
+
+cudaError_t launch_chunk_end(const ShotDev *shots_dev, int nshots,
+                             const double *partials, int nitems, int nk,
+                             unsigned *err, cudaStream_t s)
+{
+    if (nshots <= 0) return cudaSuccess;
+    k_chunk_end<<<nshots, 256, 0, s>>>(shots_dev, partials, nitems, nk, err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- checks
+
+template <class T, class CT>
+__global__ void k_check(SubDev sd, int cur, int xo, double isu, double *out)
+{
+    const double c[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0,
+                         -1.0 / 560.0};
+    const T *un = reinterpret_cast<const T *>(sd.u[cur]);
+    const T *up = reinterpret_cast<const T *>(sd.u[cur ^ 1]);
+    const CT *cf = reinterpret_cast<const CT *>(sd.coef);
+    size_t npl = (size_t)sd.nx * sd.ny;
+    size_t n = npl * sd.nz;
+    double a0 = 0, a1 = 0, a2 = 0;
+    const long long sx = 1, sy = sd.px, sz = (long long)sd.px * sd.py;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % sd.nx);
+        int y = (int)((i / sd.nx) % sd.ny);
+        int z = (int)(i / npl);
+        size_t p = pidx(sd, xo, x, y, z);
+        double u = to_d<T>(un[p]) * isu;
+        double v = to_d<T>(up[p]) * isu;
+        double lap = 3.0 * c[0] * v;
+        for (int m = 1; m <= 4; ++m)
+            lap += c[m] * (to_d<T>(up[p - m * sx]) + to_d<T>(up[p + m * sx]) +
+                           to_d<T>(up[p - m * sy]) + to_d<T>(up[p + m * sy]) +
+                           to_d<T>(up[p - m * sz]) + to_d<T>(up[p + m * sz])) * isu;
+        double d = u - v;
+        a0 += u * u;
+        a1 += d * d / to_d<CT>(cf[p]);
+        a2 += u * lap;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out + 0, a0);
+        atomicAdd(out + 1, a1);
+        atomicAdd(out + 2, a2);
+    }
+}
+
+cudaError_t launch_check(const SubDev &sd, int cur, int dtype, double scale_u,
+                         double *out, cudaStream_t s)
+{
+    size_t n = (size_t)sd.nx * sd.ny * sd.nz;
+    int g = grid_for(n);
+    int xo = dtype_xoff(dtype);
+    double isu = 1.0 / scale_u;
+    switch (dtype) {
+    case DT_F32: k_check<float, float><<<g, 256, 0, s>>>(sd, cur, xo, isu, out); break;
+    case DT_F64: k_check<double, double><<<g, 256, 0, s>>>(sd, cur, xo, isu, out); break;
+    case DT_F16S: k_check<__half, __half><<<g, 256, 0, s>>>(sd, cur, xo, isu, out); break;
+    case DT_BF16: k_check<__nv_bfloat16, __half><<<g, 256, 0, s>>>(sd, cur, xo, isu, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gw

@@ -1,0 +1,1138 @@
+// domain.cpp -- one shot decomposed into subdomains that live in one HBM:
+// PGAS allocation of the fields (paper section 3.2), the halo plan of
+// Listing 1 (section 4.5), TMA tensor maps, the work-item schedule, CUDA
+// graph chunks of K steps, model/source/receiver set-up and host I/O.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "gw_internal.h"
+
+using namespace gw;
+
+namespace {
+
+constexpr int kDefaultChunk = 25;
+constexpr size_t kStageBytes = size_t(256) << 20;   // host<->device slabs
+
+// FP64 host precompute of the scheme's constants (the library's own; the
+// scheme is not printed in the paper).
+double symbol_at_pi()
+{
+    const double c[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0,
+                         -1.0 / 560.0};
+    double s = c[0];
+    for (int m = 1; m <= 4; ++m) s += 2.0 * c[m] * ((m & 1) ? -1.0 : 1.0);
+    return s;
+}
+
+double nu_limit() { return std::sqrt(4.0 / (3.0 * std::fabs(symbol_at_pi()))); }
+
+// Cerjan factor for cell i of n with a layer of w cells and constant a.
+double cerjan(int i, int n, int w, double a)
+{
+    int d = std::min(i, n - 1 - i);
+    if (d >= w) return 1.0;
+    double e = a * (double)(w - d);
+    return std::exp(-e * e);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+CUtensorMapDataType tma_type(int elem_size, bool bf16)
+{
+    switch (elem_size) {
+    case 8: return CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    case 4: return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    default: return bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    }
+}
+
+}  // namespace
+
+struct gw_domain {
+    gw_ctx *ctx = nullptr;
+    gw_shot_desc desc{};
+    int dtype = DT_F32;
+    bool delta = false;
+    int np[3] = {1, 1, 1};
+    bool symmetric = true;
+    std::vector<int> split[3];
+    std::vector<SubDev> subs;
+    std::vector<gw_gptr> allocs;          // every allocation we own
+    gw_gptr g_fields[4] = {0, 0, 0, 0};   // u0, u1, w, coef
+    size_t device_bytes = 0;
+    // device metadata
+    SubDev *d_subs = nullptr;
+    ShotDev *d_shot = nullptr;
+    char *d_maps = nullptr;
+    unsigned *d_err = nullptr;
+    int *d_step = nullptr;
+    double *d_scratch = nullptr;          // 4 doubles for checks
+    float *d_wavelet = nullptr;
+    double *d_norms = nullptr;
+    float *d_gtab = nullptr;              // gx | gy | gz
+    int4 *d_src = nullptr;
+    int4 *d_rec = nullptr;
+    float *d_traces = nullptr;
+    Item *d_items = nullptr;
+    double *d_partials = nullptr;
+    HaloDesc *d_halo = nullptr;
+    gw_gptr g_rec = 0, g_traces = 0, g_items = 0;
+    ShotDev shot{};
+    // schedule
+    int cfg = 0;
+    TileInfo ti{};
+    int grid = 0, nitems = 0, chunk = kDefaultChunk, zc = 0;
+    std::vector<Item> items;
+    std::vector<HaloDesc> halo;
+    long long halo_total = 0;
+    // sources and receivers (host copies)
+    std::vector<int4> srcs;
+    int nrec = 0;
+    // model
+    double dt = 0, vmax = 0, courant = 0;
+    bool model_set = false;
+    double su = 1, sw = 1;
+    int step = 0;                         // steps enqueued
+    cudaStream_t last = nullptr;
+    // graphs
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_step, ev_halo;
+    double acc_ms = 0, acc_halo_ms = 0;
+    int acc_n = 0;
+
+    int nsub() const { return (int)subs.size(); }
+    int esize() const { return dtype_size(dtype); }
+};
+
+namespace {
+
+gw_status fetch_err(gw_domain *d)
+{
+    unsigned e = 0;
+    GW_TRY_CUDA(cudaMemcpy(&e, d->d_err, sizeof e, cudaMemcpyDeviceToHost));
+    if (!e) return GW_OK;
+    unsigned z = 0;
+    GW_TRY_CUDA(cudaMemcpy(d->d_err, &z, sizeof z, cudaMemcpyHostToDevice));
+    if (e & ERRB_TIMEOUT)
+        return fail(GW_ERR_TIMEOUT, "a device wait gave up (error bits 0x%x)", e);
+    if (e & ERRB_NONFINITE)
+        return fail(GW_ERR_NUMERIC, "non-finite wavefield norm (error bits 0x%x)", e);
+    return fail(GW_ERR_STATE, "device error bits 0x%x", e);
+}
+
+gw_status sync_dom(gw_domain *d)
+{
+    GW_TRY_CUDA(cudaSetDevice(d->ctx->device));
+    GW_TRY_CUDA(cudaDeviceSynchronize());
+    return fetch_err(d);
+}
+
+gw_status local_alloc(gw_domain *d, size_t bytes, char **p, gw_gptr *g = nullptr)
+{
+    gw_gptr h = 0;
+    GW_TRY(ctx_alloc_local(d->ctx, 0, bytes, &h, p));
+    d->allocs.push_back(h);
+    d->device_bytes += align_up(bytes, kAlign);
+    if (g) *g = h;
+    return GW_OK;
+}
+
+void drop_alloc(gw_domain *d, gw_gptr g)
+{
+    if (!g) return;
+    auto it = std::find(d->allocs.begin(), d->allocs.end(), g);
+    if (it != d->allocs.end()) d->allocs.erase(it);
+    ctx_free(d->ctx, g);
+}
+
+// Encode one 3-D tensor map over a padded field array.
+gw_status encode_map(gw_domain *d, CUtensorMap *out, char *base, const SubDev &s,
+                     int esize, bool bf16, int box_x, int box_y)
+{
+    auto fn = encode_fn();
+    if (!fn) return fail(GW_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[3] = {(cuuint64_t)s.px, (cuuint64_t)s.py,
+                          (cuuint64_t)(s.nz + 2 * R)};
+    cuuint64_t strides[2] = {(cuuint64_t)s.px * esize,
+                             (cuuint64_t)s.px * s.py * esize};
+    cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(out, tma_type(esize, bf16), 3, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(GW_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    (void)d;
+    return GW_OK;
+}
+
+// Work items in z-chunk-major order; the chunk size balances rounds of
+// `grid` CTAs against the 8 extra planes every item streams.
+void build_items(gw_domain *d)
+{
+    const int TX = d->ti.tx, TY = d->ti.ty;
+    long long ncols = 0;
+    int nzmax = 0;
+    for (const SubDev &s : d->subs) {
+        ncols += (long long)((s.nx + TX - 1) / TX) * ((s.ny + TY - 1) / TY);
+        nzmax = std::max(nzmax, s.nz);
+    }
+    int zc = d->desc.zchunk;
+    if (zc <= 0) {
+        double best = 1e300;
+        int best_n = 1;
+        for (int nzc = 1; nzc <= std::max(1, nzmax / 4); ++nzc) {
+            long long items = ncols * nzc;
+            long long rounds = (items + d->grid - 1) / d->grid;
+            double cost = (double)rounds * ((double)nzmax / nzc + 8 * 0.3);
+            if (cost < best - 1e-9) {
+                best = cost;
+                best_n = nzc;
+            }
+        }
+        zc = (nzmax + best_n - 1) / best_n;
+    }
+    d->zc = zc;
+    struct Key { int z, sub, y, x; };
+    std::vector<std::pair<Key, Item>> v;
+    for (int si = 0; si < d->nsub(); ++si) {
+        const SubDev &s = d->subs[si];
+        int nzc = (s.nz + zc - 1) / zc;
+        for (int c = 0; c < nzc; ++c) {
+            int z0 = (int)((long long)s.nz * c / nzc);
+            int z1 = (int)((long long)s.nz * (c + 1) / nzc);
+            if (z1 <= z0) continue;
+            for (int y0 = 0; y0 < s.ny; y0 += TY)
+                for (int x0 = 0; x0 < s.nx; x0 += TX) {
+                    Item it{si, x0 | (y0 << 16), z0, z1};
+                    v.push_back({Key{s.gz0 + z0, si, y0, x0}, it});
+                }
+        }
+    }
+    std::stable_sort(v.begin(), v.end(), [](const auto &a, const auto &b) {
+        if (a.first.z != b.first.z) return a.first.z < b.first.z;
+        if (a.first.sub != b.first.sub) return a.first.sub < b.first.sub;
+        if (a.first.y != b.first.y) return a.first.y < b.first.y;
+        return a.first.x < b.first.x;
+    });
+    d->items.clear();
+    for (auto &p : v) d->items.push_back(p.second);
+    d->nitems = (int)d->items.size();
+}
+
+void build_halo_plan(gw_domain *d)
+{
+    d->halo.clear();
+    long long tot = 0;
+    for (int si = 0; si < d->nsub(); ++si) {
+        const SubDev &s = d->subs[si];
+        for (int f = 0; f < 6; ++f) {
+            int nb = s.nbr[f];
+            if (nb < 0) continue;
+            long long cnt = (f >> 1) == 0 ? (long long)R * s.ny * s.nz
+                          : (f >> 1) == 1 ? (long long)s.nx * R * s.nz
+                                          : (long long)s.nx * s.ny * R;
+            HaloDesc h{si, nb, f, 0, tot};
+            d->halo.push_back(h);
+            tot += cnt;
+        }
+    }
+    d->halo_total = tot;
+}
+
+gw_status plan_schedule(gw_domain *d)
+{
+    gw_ctx *c = d->ctx;
+    int ncfg = step_cfg_count(d->dtype);
+    int want = d->desc.tile > 0 ? d->desc.tile - 1 : 0;
+    if (want >= ncfg) return fail(GW_ERR_ARG, "tile %d not available", d->desc.tile);
+    d->cfg = want;
+    step_cfg_info(d->dtype, d->cfg, &d->ti);
+    bool sponge = d->desc.sponge > 0;
+    int occ = step_cfg_occupancy(d->dtype, d->cfg, sponge);
+    if (occ <= 0) return fail(GW_ERR_CUDA, "kernel configuration does not fit an SM");
+    d->grid = std::max(1, c->num_sms * occ);
+    build_items(d);
+    if (d->nitems == 0) return fail(GW_ERR_ARG, "empty grid");
+    d->grid = std::min(d->grid, d->nitems);
+    // items and the norm partials of one chunk
+    if (d->g_items) drop_alloc(d, d->g_items);
+    size_t ib = sizeof(Item) * d->nitems;
+    size_t pb = sizeof(double) * (size_t)d->nitems * (size_t)std::max(1, d->chunk);
+    char *p = nullptr;
+    GW_TRY(local_alloc(d, ib + pb + kAlign, &p, &d->g_items));
+    d->d_items = reinterpret_cast<Item *>(p);
+    d->d_partials = reinterpret_cast<double *>(p + align_up(ib, kAlign));
+    GW_TRY_CUDA(cudaMemcpy(d->d_items, d->items.data(), ib, cudaMemcpyHostToDevice));
+    d->shot.first_item = 0;
+    d->shot.nitems = d->nitems;
+    return GW_OK;
+}
+
+gw_status push_shot(gw_domain *d)
+{
+    GW_TRY_CUDA(cudaMemcpy(d->d_shot, &d->shot, sizeof(ShotDev), cudaMemcpyHostToDevice));
+    return GW_OK;
+}
+
+gw_status make_maps(gw_domain *d)
+{
+    const int es = d->esize();
+    const int xo = dtype_xoff(d->dtype);
+    const bool bf16 = d->dtype == DT_BF16;
+    std::vector<CUtensorMap> maps((size_t)d->nsub() * kMapsPerSub);
+    std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+    for (int si = 0; si < d->nsub(); ++si) {
+        const SubDev &s = d->subs[si];
+        CUtensorMap *m = &maps[(size_t)si * kMapsPerSub];
+        int hx = d->ti.tx + 2 * xo, hy = d->ti.ty + 2 * R;
+        GW_TRY(encode_map(d, &m[MAP_U0_HALO], s.u[0], s, es, bf16, hx, hy));
+        GW_TRY(encode_map(d, &m[MAP_U1_HALO], s.u[1], s, es, bf16, hx, hy));
+        GW_TRY(encode_map(d, &m[MAP_U0_PW], s.u[0], s, es, bf16, d->ti.tx, d->ti.ty));
+        GW_TRY(encode_map(d, &m[MAP_U1_PW], s.u[1], s, es, bf16, d->ti.tx, d->ti.ty));
+        // reduced storage keeps coef in FP16
+        int ces = d->delta ? 2 : es;
+        GW_TRY(encode_map(d, &m[MAP_COEF_PW], s.coef, s, ces, false, d->ti.tx, d->ti.ty));
+        if (d->delta)
+            GW_TRY(encode_map(d, &m[MAP_W_PW], s.w, s, es, bf16, d->ti.tx, d->ti.ty));
+    }
+    GW_TRY_CUDA(cudaMemcpy(d->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
+                           cudaMemcpyHostToDevice));
+    return GW_OK;
+}
+
+void destroy_graph(gw_domain *d)
+{
+    if (d->gexec) cudaGraphExecDestroy(d->gexec);
+    d->gexec = nullptr;
+}
+
+StepArgs step_args(gw_domain *d, int k)
+{
+    StepArgs a{};
+    a.subs = d->d_subs;
+    a.shots = d->d_shot;
+    a.items = d->d_items;
+    a.maps = d->d_maps;
+    a.partials = d->d_partials;
+    a.err = d->d_err;
+    a.seg_base = d->ctx->base;
+    a.rank_stride = (long long)d->ctx->rank_bytes;
+    a.nitems = d->nitems;
+    a.k = k;
+    a.symmetric = d->symmetric ? 1 : 0;
+    a.fused_halo = d->desc.halo_mode == GW_HALO_FUSED ? 1 : 0;
+    return a;
+}
+
+cudaEvent_t pool_event(gw_domain *d)
+{
+    if (!d->ev_pool.empty()) {
+        cudaEvent_t e = d->ev_pool.back();
+        d->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Enqueue nk steps (k = 0..nk-1) and the chunk end.
+gw_status enqueue_chunk(gw_domain *d, int nk, cudaStream_t s, bool timed)
+{
+    const bool sponge = d->desc.sponge > 0;
+    const bool sep = d->desc.halo_mode == GW_HALO_SEPARATE && !d->halo.empty();
+    for (int k = 0; k < nk; ++k) {
+        StepArgs a = step_args(d, k);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (timed) {
+            e0 = pool_event(d);
+            e1 = pool_event(d);
+            GW_TRY_CUDA(cudaEventRecord(e0, s));
+        }
+        GW_TRY_CUDA(launch_step(d->dtype, d->cfg, sponge, d->grid, a, s));
+        if (timed) {
+            GW_TRY_CUDA(cudaEventRecord(e1, s));
+            d->ev_step.push_back({e0, e1});
+        }
+        if (sep) {
+            cudaEvent_t h0 = nullptr, h1 = nullptr;
+            if (timed) {
+                h0 = pool_event(d);
+                h1 = pool_event(d);
+                GW_TRY_CUDA(cudaEventRecord(h0, s));
+            }
+            GW_TRY_CUDA(launch_halo(d->d_halo, (int)d->halo.size(), d->halo_total,
+                                    d->d_subs, d->d_step, k, d->dtype, s));
+            if (timed) {
+                GW_TRY_CUDA(cudaEventRecord(h1, s));
+                d->ev_halo.push_back({h0, h1});
+            }
+        }
+    }
+    GW_TRY_CUDA(launch_chunk_end(d->d_shot, 1, d->d_partials, d->nitems, nk,
+                                 d->d_err, s));
+    return GW_OK;
+}
+
+gw_status ensure_graph(gw_domain *d)
+{
+    if (d->gexec) return GW_OK;
+    if (!d->cap_stream)
+        GW_TRY_CUDA(cudaStreamCreateWithFlags(&d->cap_stream, cudaStreamNonBlocking));
+    GW_TRY_CUDA(cudaStreamBeginCapture(d->cap_stream, cudaStreamCaptureModeThreadLocal));
+    gw_status st = enqueue_chunk(d, d->chunk, d->cap_stream, false);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(d->cap_stream, &g);
+    if (st != GW_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&d->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return GW_OK;
+}
+
+void harvest_events(gw_domain *d)
+{
+    for (auto &p : d->ev_step) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) {
+            d->acc_ms += ms;
+            ++d->acc_n;
+        }
+        d->ev_pool.push_back(p.first);
+        d->ev_pool.push_back(p.second);
+    }
+    for (auto &p : d->ev_halo) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess)
+            d->acc_halo_ms += ms;
+        d->ev_pool.push_back(p.first);
+        d->ev_pool.push_back(p.second);
+    }
+    d->ev_step.clear();
+    d->ev_halo.clear();
+}
+
+// Dense slab staging buffer (device), allocated per call.
+struct Stage {
+    gw_domain *d;
+    gw_gptr g = 0;
+    char *p = nullptr;
+    size_t bytes = 0;
+    ~Stage() { if (g) drop_alloc(d, g); }
+};
+
+gw_status stage_alloc(gw_domain *d, Stage &st, size_t want, size_t plane_bytes)
+{
+    st.d = d;
+    // at least one plane, at most kStageBytes unless a plane is larger
+    st.bytes = std::max(std::min(want, kStageBytes), plane_bytes + 16);
+    return local_alloc(d, st.bytes, &st.p, &st.g);
+}
+
+int planes_per_slab(const gw_domain *d, size_t bytes_per_elem, size_t stage)
+{
+    size_t plane = (size_t)d->desc.nx * d->desc.ny * bytes_per_elem;
+    return (int)std::max<size_t>(1, stage / plane);
+}
+
+gw_status check_dom(gw_domain *d)
+{
+    if (!d) return fail(GW_ERR_ARG, "domain is NULL");
+    if (d->ctx->device < 0) return fail(GW_ERR_STATE, "host-only context cannot run kernels");
+    GW_TRY_CUDA(cudaSetDevice(d->ctx->device));
+    return GW_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+
+extern "C" {
+
+gw_status gw_domain_create(gw_ctx *c, const gw_shot_desc *desc, int px, int py,
+                           int pz, const int *split_x, const int *split_y,
+                           const int *split_z, int symmetric, gw_domain **out)
+{
+    if (!c || !desc || !out) return fail(GW_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (c->device < 0) return fail(GW_ERR_STATE, "domains need a device context");
+    if (!c->base) return fail(GW_ERR_STATE, "no segment attached");
+    const gw_shot_desc &D = *desc;
+    if (D.nx <= 0 || D.ny <= 0 || D.nz <= 0 || D.h <= 0 || D.nsteps < 0)
+        return fail(GW_ERR_ARG, "bad grid %d x %d x %d, h %g", D.nx, D.ny, D.nz, D.h);
+    if (D.nx > 65535 || D.ny > 65535)
+        return fail(GW_ERR_ARG, "nx, ny must be < 65536");
+    if (D.dtype < DT_F32 || D.dtype > DT_BF16) return fail(GW_ERR_ARG, "bad dtype");
+    if (px <= 0 || py <= 0 || pz <= 0) return fail(GW_ERR_ARG, "bad decomposition");
+    int nsub = px * py * pz;
+    if (nsub > c->nranks)
+        return fail(GW_ERR_ARG, "%d subdomains need %d ranks; the segment has %d",
+                    nsub, nsub, c->nranks);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    GW_TRY_CUDA(cudaSetDevice(c->device));
+
+    gw_domain *d = new (std::nothrow) gw_domain();
+    if (!d) return fail(GW_ERR_NOMEM, "out of host memory");
+    d->ctx = c;
+    d->desc = D;
+    if (d->desc.sponge_a <= 0) d->desc.sponge_a = 0.015;
+    d->dtype = D.dtype;
+    d->delta = D.dtype == DT_F16S || D.dtype == DT_BF16;
+    d->np[0] = px; d->np[1] = py; d->np[2] = pz;
+    d->symmetric = symmetric != 0;
+    d->chunk = D.chunk == 0 ? kDefaultChunk : std::max(1, std::abs(D.chunk));
+
+    auto fail_out = [&](gw_status st) {
+        gw_domain_destroy(d);
+        return st;
+    };
+
+    // ---- decomposition (tensor-product split, rank = (k*py + j)*px + i)
+    const int *splits[3] = {split_x, split_y, split_z};
+    const int ext[3] = {D.nx, D.ny, D.nz};
+    for (int a = 0; a < 3; ++a) {
+        int n = ext[a], p = d->np[a];
+        d->split[a].assign(p, 0);
+        long long sum = 0;
+        for (int i = 0; i < p; ++i) {
+            int v = splits[a] ? splits[a][i] : n / p + (i < n % p ? 1 : 0);
+            if (v <= 0) return fail_out(fail(GW_ERR_ARG, "empty subdomain along axis %d", a));
+            if (v < R && (p > 1 || (D.periodic >> a & 1)))
+                return fail_out(fail(GW_ERR_ARG, "subdomain thinner than the halo"));
+            d->split[a][i] = v;
+            sum += v;
+        }
+        if (sum != n) return fail_out(fail(GW_ERR_ARG, "splits of axis %d do not sum to %d", a, n));
+    }
+    const int es = dtype_size(d->dtype), xo = dtype_xoff(d->dtype);
+    const int cmul = 128 / es;   // row pitch: a multiple of 128 bytes
+    d->subs.assign(nsub, SubDev{});
+    int maxn[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a)
+        for (int v : d->split[a]) maxn[a] = std::max(maxn[a], v);
+    std::vector<size_t> fbytes(nsub), cbytes(nsub);
+    for (int k = 0, gz = 0; k < pz; gz += d->split[2][k], ++k)
+        for (int j = 0, gy = 0; j < py; gy += d->split[1][j], ++j)
+            for (int i = 0, gx = 0; i < px; gx += d->split[0][i], ++i) {
+                int r = (k * py + j) * px + i;
+                SubDev &s = d->subs[r];
+                s.nx = d->split[0][i]; s.ny = d->split[1][j]; s.nz = d->split[2][k];
+                s.gx0 = gx; s.gy0 = gy; s.gz0 = gz;
+                // symmetric: every subdomain laid out like the largest one
+                int lx = d->symmetric ? maxn[0] : s.nx;
+                int ly = d->symmetric ? maxn[1] : s.ny;
+                int lz = d->symmetric ? maxn[2] : s.nz;
+                s.px = (int)align_up((size_t)(xo + lx + R), (size_t)cmul);
+                s.py = ly + 2 * R;
+                s.shot = 0;
+                s.rank = r;
+                size_t elems = (size_t)s.px * s.py * (size_t)(lz + 2 * R);
+                fbytes[r] = elems * es;
+                cbytes[r] = elems * (d->delta ? 2 : es);
+                int ii[3] = {i, j, k};
+                for (int a = 0; a < 3; ++a)
+                    for (int side = 0; side < 2; ++side) {
+                        int q[3] = {ii[0], ii[1], ii[2]};
+                        q[a] += side ? 1 : -1;
+                        bool wrap = (D.periodic >> a) & 1;
+                        if (q[a] < 0 || q[a] >= d->np[a]) {
+                            if (!wrap) { s.nbr[2 * a + side] = -1; continue; }
+                            q[a] = (q[a] + d->np[a]) % d->np[a];
+                        }
+                        s.nbr[2 * a + side] = (q[2] * py + q[1]) * px + q[0];
+                    }
+            }
+
+    // ---- PGAS allocation of the fields
+    const int nf = d->delta ? 4 : 3;
+    const int fields[4] = {0, 1, 3, 2};   // u0, u1, coef, (w)
+    for (int fi = 0; fi < nf; ++fi) {
+        int f = fields[fi];
+        gw_gptr g = 0;
+        gw_status st;
+        if (d->symmetric) {
+            size_t b = f == 3 ? cbytes[0] : fbytes[0];
+            st = ctx_alloc_sym(c, b, &g);
+            if (st == GW_OK) d->device_bytes += align_up(b, kAlign) * nsub;
+        } else {
+            std::vector<size_t> b(c->nranks, 0);
+            for (int r = 0; r < nsub; ++r) b[r] = f == 3 ? cbytes[r] : fbytes[r];
+            st = ctx_alloc_asym(c, b.data(), &g);
+            if (st == GW_OK)
+                for (int r = 0; r < nsub; ++r) d->device_bytes += align_up(b[r], kAlign);
+        }
+        if (st != GW_OK) return fail_out(st);
+        d->allocs.push_back(g);
+        d->g_fields[f] = g;
+        for (int r = 0; r < nsub; ++r) {
+            char *p = nullptr;
+            size_t sz = 0;
+            // asymmetric: a second-level pointer fetch, then the cache
+            gw_status rs = ctx_resolve(c, g, r, &p, &sz);
+            if (rs != GW_OK) return fail_out(rs);
+            cudaError_t e = cudaMemset(p, 0, sz);
+            if (e != cudaSuccess) return fail_out(cuda_fail(e, "cudaMemset"));
+            SubDev &s = d->subs[r];
+            if (f == 0) s.u[0] = p;
+            else if (f == 1) s.u[1] = p;
+            else if (f == 2) s.w = p;
+            else s.coef = p;
+        }
+    }
+
+    // ---- metadata
+    const int cap = std::max(1, D.nsteps);
+    size_t off_subs = 0;
+    size_t off_shot = align_up(off_subs + sizeof(SubDev) * nsub, kAlign);
+    size_t off_maps = align_up(off_shot + sizeof(ShotDev), kAlign);
+    size_t off_err = align_up(off_maps + 128 * kMapsPerSub * (size_t)nsub, kAlign);
+    size_t off_step = off_err + 64;
+    size_t off_scr = off_err + 128;
+    size_t off_wl = align_up(off_scr + 64, kAlign);
+    size_t off_norm = align_up(off_wl + sizeof(float) * kMaxSources * (size_t)cap, kAlign);
+    size_t off_g = align_up(off_norm + sizeof(double) * (size_t)cap, kAlign);
+    size_t off_src = align_up(off_g + sizeof(float) * (size_t)(D.nx + D.ny + D.nz), kAlign);
+    size_t off_halo = align_up(off_src + sizeof(int4) * kMaxSources, kAlign);
+    size_t total = align_up(off_halo + sizeof(HaloDesc) * 6 * (size_t)nsub, kAlign);
+    char *m = nullptr;
+    gw_status st = local_alloc(d, total, &m);
+    if (st != GW_OK) return fail_out(st);
+    cudaError_t e = cudaMemset(m, 0, total);
+    if (e != cudaSuccess) return fail_out(cuda_fail(e, "cudaMemset"));
+    d->d_subs = reinterpret_cast<SubDev *>(m + off_subs);
+    d->d_shot = reinterpret_cast<ShotDev *>(m + off_shot);
+    d->d_maps = m + off_maps;
+    d->d_err = reinterpret_cast<unsigned *>(m + off_err);
+    d->d_step = reinterpret_cast<int *>(m + off_step);
+    d->d_scratch = reinterpret_cast<double *>(m + off_scr);
+    d->d_wavelet = reinterpret_cast<float *>(m + off_wl);
+    d->d_norms = reinterpret_cast<double *>(m + off_norm);
+    d->d_gtab = reinterpret_cast<float *>(m + off_g);
+    d->d_src = reinterpret_cast<int4 *>(m + off_src);
+    d->d_halo = reinterpret_cast<HaloDesc *>(m + off_halo);
+
+    // sponge tables on global coordinates, FP64 -> FP32
+    {
+        std::vector<float> g(D.nx + D.ny + D.nz);
+        const int n3[3] = {D.nx, D.ny, D.nz};
+        size_t o = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int i = 0; i < n3[a]; ++i)
+                g[o++] = (float)cerjan(i, n3[a], D.sponge, d->desc.sponge_a);
+        e = cudaMemcpy(d->d_gtab, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail_out(cuda_fail(e, "cudaMemcpy"));
+    }
+    ShotDev &sh = d->shot;
+    sh.step = d->d_step;
+    sh.wavelet = d->d_wavelet;
+    sh.traces = nullptr;
+    sh.norms = d->d_norms;
+    sh.gx = d->d_gtab;
+    sh.gy = d->d_gtab + D.nx;
+    sh.gz = d->d_gtab + D.nx + D.ny;
+    sh.src = d->d_src;
+    sh.rec = nullptr;
+    sh.cap = cap;
+    sh.nsrc = 0;
+    sh.nrec = 0;
+    sh.NX = D.nx; sh.NY = D.ny; sh.NZ = D.nz;
+    sh.su = sh.sw = sh.isu = sh.isw = 1.0f;
+
+    e = cudaMemcpy(d->d_subs, d->subs.data(), sizeof(SubDev) * nsub, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail_out(cuda_fail(e, "cudaMemcpy"));
+    build_halo_plan(d);
+    if (!d->halo.empty()) {
+        e = cudaMemcpy(d->d_halo, d->halo.data(), sizeof(HaloDesc) * d->halo.size(),
+                       cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail_out(cuda_fail(e, "cudaMemcpy"));
+    }
+    st = plan_schedule(d);
+    if (st != GW_OK) return fail_out(st);
+    st = make_maps(d);
+    if (st != GW_OK) return fail_out(st);
+    st = push_shot(d);
+    if (st != GW_OK) return fail_out(st);
+    *out = d;
+    return GW_OK;
+}
+
+gw_status gw_domain_destroy(gw_domain *d)
+{
+    if (!d) return GW_OK;
+    gw_ctx *c = d->ctx;
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    if (c->device >= 0) {
+        cudaSetDevice(c->device);
+        cudaDeviceSynchronize();
+    }
+    destroy_graph(d);
+    if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
+    harvest_events(d);
+    for (cudaEvent_t e : d->ev_pool) cudaEventDestroy(e);
+    for (gw_gptr g : d->allocs) ctx_free(c, g);
+    delete d;
+    return GW_OK;
+}
+
+gw_status gw_domain_info_get(gw_domain *d, gw_domain_info *out)
+{
+    if (!d || !out) return fail(GW_ERR_ARG, "NULL argument");
+    out->dt = d->dt;
+    out->courant = d->courant;
+    out->vmax = d->vmax;
+    out->nsub = d->nsub();
+    out->step = d->step;
+    out->tile = d->cfg + 1;
+    out->ctas = d->grid;
+    out->items = d->nitems;
+    out->scale_u = d->su;
+    out->scale_w = d->sw;
+    out->device_bytes = d->device_bytes;
+    return GW_OK;
+}
+
+static void choose_scales(gw_domain *d);
+
+static gw_status set_model_impl(gw_domain *d, const void *vel, bool f32)
+{
+    GW_TRY(check_dom(d));
+    if (!vel) return fail(GW_ERR_ARG, "vel is NULL");
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    GW_TRY(sync_dom(d));
+    const gw_shot_desc &D = d->desc;
+    const size_t vs = f32 ? 4 : 8;
+    const size_t plane = (size_t)D.nx * D.ny;
+    Stage st;
+    GW_TRY(stage_alloc(d, st, plane * D.nz * vs + 16, plane * vs));
+    int pps = planes_per_slab(d, vs, st.bytes - 16);
+    unsigned long long *d_max = reinterpret_cast<unsigned long long *>(d->d_scratch);
+    GW_TRY_CUDA(cudaMemset(d_max, 0, sizeof *d_max));
+    const char *h = static_cast<const char *>(vel);
+    // pass 1: vmax on the GPU
+    for (int z = 0; z < D.nz; z += pps) {
+        int zh = std::min(D.nz, z + pps);
+        size_t b = plane * (size_t)(zh - z) * vs;
+        GW_TRY_CUDA(cudaMemcpy(st.p, h + plane * (size_t)z * vs, b, cudaMemcpyHostToDevice));
+        GW_TRY_CUDA(launch_vmax(st.p, plane * (size_t)(zh - z), f32, d_max, nullptr));
+    }
+    unsigned long long bits = 0;
+    GW_TRY_CUDA(cudaMemcpy(&bits, d_max, sizeof bits, cudaMemcpyDeviceToHost));
+    double vmax;
+    std::memcpy(&vmax, &bits, sizeof vmax);
+    if (!(vmax > 0) || !std::isfinite(vmax))
+        return fail(GW_ERR_ARG, "velocity model must be positive and finite");
+    d->vmax = vmax;
+    if (D.dt > 0) {
+        d->dt = D.dt;
+    } else {
+        double nu = D.courant > 0 ? D.courant : 0.5 * nu_limit();
+        d->dt = nu * D.h / vmax;
+    }
+    d->courant = vmax * d->dt / D.h;
+    // pass 2: coef = (v dt / h)^2 in FP64 on the GPU, rounded to storage
+    for (int z = 0; z < D.nz; z += pps) {
+        int zh = std::min(D.nz, z + pps);
+        size_t b = plane * (size_t)(zh - z) * vs;
+        GW_TRY_CUDA(cudaMemcpy(st.p, h + plane * (size_t)z * vs, b, cudaMemcpyHostToDevice));
+        ModelSlab ms{st.p, f32 ? 1 : 0, D.nx, D.ny, z, zh, d->dt / D.h};
+        for (const SubDev &s : d->subs)
+            GW_TRY_CUDA(launch_coef(ms, s, d->dtype, nullptr));
+    }
+    GW_TRY_CUDA(cudaDeviceSynchronize());
+    d->model_set = true;
+    choose_scales(d);
+    return push_shot(d);
+}
+
+gw_status gw_set_model(gw_domain *d, const double *vel) { return set_model_impl(d, vel, false); }
+gw_status gw_set_model_f32(gw_domain *d, const float *vel) { return set_model_impl(d, vel, true); }
+
+gw_status gw_ricker(double f, double dt, int n, float *out)
+{
+    if (f <= 0 || dt <= 0 || n < 0 || (n && !out)) return fail(GW_ERR_ARG, "bad Ricker arguments");
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) {
+        double tau = i * dt - 1.0 / f;
+        double a = pi * pi * f * f * tau * tau;
+        out[i] = (float)((1.0 - 2.0 * a) * std::exp(-a));
+    }
+    return GW_OK;
+}
+
+// Power-of-two scales of FP16 delta storage: keep the largest expected
+// |u| near 2^12 (16x headroom below the FP16 maximum) and w four times
+// larger (w ~ u * omega * dt is smaller than u).
+static void choose_scales(gw_domain *d)
+{
+    if (d->dtype != DT_F16S) {
+        d->su = d->sw = 1.0;
+    } else {
+        double amp = 0.0;
+        const double cmax = d->courant * d->courant;
+        for (size_t s = 0; s < d->srcs.size(); ++s) {
+            double acc = 0.0;
+            // sum of |wavelet| bounds the accumulated kick at the source
+            std::vector<float> w(d->shot.cap);
+            cudaMemcpy(w.data(), d->d_wavelet + s * d->shot.cap,
+                       sizeof(float) * d->shot.cap, cudaMemcpyDeviceToHost);
+            for (float v : w) acc += std::fabs((double)v);
+            amp += cmax * acc;
+        }
+        if (amp <= 0) amp = 1.0;
+        double k = std::floor(std::log2(4096.0 / amp));
+        k = std::max(-20.0, std::min(20.0, k));
+        d->su = std::ldexp(1.0, (int)k);
+        d->sw = d->su * 4.0;
+        if (d->desc.scale_u > 0) d->su = d->desc.scale_u;
+        if (d->desc.scale_w > 0) d->sw = d->desc.scale_w;
+    }
+    d->shot.su = (float)d->su;
+    d->shot.sw = (float)d->sw;
+    d->shot.isu = (float)(1.0 / d->su);
+    d->shot.isw = (float)(1.0 / d->sw);
+}
+
+gw_status gw_inject_source(gw_domain *d, int gx, int gy, int gz,
+                           const float *wavelet, int n)
+{
+    GW_TRY(check_dom(d));
+    const gw_shot_desc &D = d->desc;
+    if (gx < 0 || gy < 0 || gz < 0 || gx >= D.nx || gy >= D.ny || gz >= D.nz)
+        return fail(GW_ERR_ARG, "source (%d, %d, %d) outside the grid", gx, gy, gz);
+    if ((int)d->srcs.size() >= kMaxSources) return fail(GW_ERR_ARG, "too many sources");
+    if (n < 0 || (n && !wavelet)) return fail(GW_ERR_ARG, "bad wavelet");
+    if (d->step != 0 && d->dtype == DT_F16S)
+        return fail(GW_ERR_STATE, "FP16 scales are fixed once stepping started");
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    GW_TRY(sync_dom(d));
+    int idx = (int)d->srcs.size();
+    std::vector<float> w(d->shot.cap, 0.0f);
+    for (int i = 0; i < std::min(n, d->shot.cap); ++i) w[i] = wavelet[i];
+    GW_TRY_CUDA(cudaMemcpy(d->d_wavelet + (size_t)idx * d->shot.cap, w.data(),
+                           sizeof(float) * w.size(), cudaMemcpyHostToDevice));
+    d->srcs.push_back(make_int4(gx, gy, gz, 0));
+    GW_TRY_CUDA(cudaMemcpy(d->d_src, d->srcs.data(), sizeof(int4) * d->srcs.size(),
+                           cudaMemcpyHostToDevice));
+    d->shot.nsrc = (int)d->srcs.size();
+    choose_scales(d);
+    return push_shot(d);
+}
+
+gw_status gw_set_receivers(gw_domain *d, int nrec, const int *xyz)
+{
+    GW_TRY(check_dom(d));
+    if (nrec < 0 || (nrec && !xyz)) return fail(GW_ERR_ARG, "bad receivers");
+    const gw_shot_desc &D = d->desc;
+    std::vector<int4> r(nrec);
+    for (int i = 0; i < nrec; ++i) {
+        int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        if (x < 0 || y < 0 || z < 0 || x >= D.nx || y >= D.ny || z >= D.nz)
+            return fail(GW_ERR_ARG, "receiver %d outside the grid", i);
+        r[i] = make_int4(x, y, z, 0);
+    }
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    GW_TRY(sync_dom(d));
+    if (d->g_rec) { drop_alloc(d, d->g_rec); d->g_rec = 0; d->d_rec = nullptr; }
+    if (d->g_traces) { drop_alloc(d, d->g_traces); d->g_traces = 0; d->d_traces = nullptr; }
+    if (nrec) {
+        char *p = nullptr;
+        GW_TRY(local_alloc(d, sizeof(int4) * nrec, &p, &d->g_rec));
+        d->d_rec = reinterpret_cast<int4 *>(p);
+        GW_TRY_CUDA(cudaMemcpy(d->d_rec, r.data(), sizeof(int4) * nrec, cudaMemcpyHostToDevice));
+        size_t tb = sizeof(float) * (size_t)nrec * d->shot.cap;
+        GW_TRY(local_alloc(d, tb, &p, &d->g_traces));
+        d->d_traces = reinterpret_cast<float *>(p);
+        GW_TRY_CUDA(cudaMemset(d->d_traces, 0, tb));
+    }
+    d->nrec = nrec;
+    d->shot.nrec = nrec;
+    d->shot.rec = d->d_rec;
+    d->shot.traces = d->d_traces;
+    return push_shot(d);
+}
+
+gw_status gw_step(gw_domain *d, int nsteps, gw_stream stream)
+{
+    GW_TRY(check_dom(d));
+    if (nsteps < 0) return fail(GW_ERR_ARG, "negative step count");
+    if (!d->model_set) return fail(GW_ERR_STATE, "set the velocity model first");
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    d->last = s;
+    int left = nsteps;
+    const bool graphs = d->desc.chunk >= 0 && !d->timing;
+    while (left > 0) {
+        if (graphs && left >= d->chunk) {
+            GW_TRY(ensure_graph(d));
+            GW_TRY_CUDA(cudaGraphLaunch(d->gexec, s));
+            left -= d->chunk;
+            d->step += d->chunk;
+        } else {
+            int nk = std::min(left, d->chunk);
+            GW_TRY(enqueue_chunk(d, nk, s, d->timing));
+            left -= nk;
+            d->step += nk;
+        }
+    }
+    return GW_OK;
+}
+
+gw_status gw_put_halo(gw_domain *d, gw_stream stream)
+{
+    GW_TRY(check_dom(d));
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    if (d->halo.empty()) return GW_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    d->last = s;
+    GW_TRY_CUDA(launch_halo(d->d_halo, (int)d->halo.size(), d->halo_total, d->d_subs,
+                            d->d_step, -1, d->dtype, s));
+    return GW_OK;
+}
+
+gw_status gw_barrier(gw_domain *d, gw_stream stream, int sync)
+{
+    GW_TRY(check_dom(d));
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // puts issued on another stream become visible to `s` from here on
+    if (d->last && d->last != s) {
+        cudaEvent_t ev;
+        GW_TRY_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(ev, d->last);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+        cudaEventDestroy(ev);
+        if (e != cudaSuccess) return cuda_fail(e, "barrier join");
+    }
+    GW_TRY(gw_fence(d->ctx, stream));
+    if (sync) {
+        GW_TRY_CUDA(cudaStreamSynchronize(s));
+        return sync_dom(d);
+    }
+    return GW_OK;
+}
+
+gw_status gw_read_receivers(gw_domain *d, float *out, int nrec, int nsteps)
+{
+    GW_TRY(check_dom(d));
+    if (nrec < 0 || nrec > d->nrec || nsteps < 0 || nsteps > d->shot.cap || (!out && nrec && nsteps))
+        return fail(GW_ERR_ARG, "bad receiver read (%d of %d receivers, %d steps)", nrec,
+                    d->nrec, nsteps);
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    GW_TRY(sync_dom(d));
+    for (int r = 0; r < nrec; ++r)
+        GW_TRY_CUDA(cudaMemcpy(out + (size_t)r * nsteps, d->d_traces + (size_t)r * d->shot.cap,
+                               sizeof(float) * nsteps, cudaMemcpyDeviceToHost));
+    return GW_OK;
+}
+
+static gw_status field_index(gw_domain *d, int which, int *f, double *scale)
+{
+    *scale = 1.0;
+    switch (which) {
+    case GW_FIELD_U: *f = 0; *scale = d->su; return GW_OK;
+    case GW_FIELD_UPREV: *f = 1; *scale = d->su; return GW_OK;
+    case GW_FIELD_W:
+        if (!d->delta) return fail(GW_ERR_ARG, "GW_FIELD_W needs delta (16-bit) storage");
+        *f = 2; *scale = d->sw; return GW_OK;
+    case GW_FIELD_COEF: *f = 3; return GW_OK;
+    default: return fail(GW_ERR_ARG, "unknown field %d", which);
+    }
+}
+
+gw_status gw_read_wavefield(gw_domain *d, int which, void *out, int f64)
+{
+    GW_TRY(check_dom(d));
+    if (!out) return fail(GW_ERR_ARG, "out is NULL");
+    int f = 0;
+    double scale;
+    GW_TRY(field_index(d, which, &f, &scale));
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    GW_TRY(sync_dom(d));
+    const gw_shot_desc &D = d->desc;
+    const size_t es = f64 ? 8 : 4, plane = (size_t)D.nx * D.ny;
+    Stage st;
+    GW_TRY(stage_alloc(d, st, plane * D.nz * es, plane * es));
+    int pps = planes_per_slab(d, es, st.bytes);
+    char *h = static_cast<char *>(out);
+    for (int z = 0; z < D.nz; z += pps) {
+        int zh = std::min(D.nz, z + pps);
+        FieldSlab fs{st.p, f64, D.nx, D.ny, z, zh, f, d->step & 1, scale};
+        for (const SubDev &s : d->subs) GW_TRY_CUDA(launch_gather(fs, s, d->dtype, nullptr));
+        GW_TRY_CUDA(cudaMemcpy(h + plane * (size_t)z * es, st.p, plane * (size_t)(zh - z) * es,
+                               cudaMemcpyDeviceToHost));
+    }
+    return GW_OK;
+}
+
+gw_status gw_write_wavefield(gw_domain *d, int which, const void *in, int f64)
+{
+    GW_TRY(check_dom(d));
+    if (!in) return fail(GW_ERR_ARG, "input is NULL");
+    if (which == GW_FIELD_UPREV && d->delta)
+        return fail(GW_ERR_ARG, "delta storage: write GW_FIELD_W (w = u_n - G u_{n-1})");
+    if (which == GW_FIELD_COEF) return fail(GW_ERR_ARG, "set coef through gw_set_model");
+    int f = 0;
+    double scale;
+    GW_TRY(field_index(d, which, &f, &scale));
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    GW_TRY(sync_dom(d));
+    const gw_shot_desc &D = d->desc;
+    const size_t es = f64 ? 8 : 4, plane = (size_t)D.nx * D.ny;
+    Stage st;
+    GW_TRY(stage_alloc(d, st, plane * D.nz * es, plane * es));
+    int pps = planes_per_slab(d, es, st.bytes);
+    const char *h = static_cast<const char *>(in);
+    for (int z = 0; z < D.nz; z += pps) {
+        int zh = std::min(D.nz, z + pps);
+        GW_TRY_CUDA(cudaMemcpy(st.p, h + plane * (size_t)z * es, plane * (size_t)(zh - z) * es,
+                               cudaMemcpyHostToDevice));
+        FieldSlab fs{st.p, f64, D.nx, D.ny, z, zh, f, d->step & 1, scale};
+        for (const SubDev &s : d->subs) GW_TRY_CUDA(launch_scatter(fs, s, d->dtype, nullptr));
+    }
+    // refresh the face halos of the written field
+    if (!d->halo.empty() && (f == 0 || f == 1))
+        GW_TRY_CUDA(launch_halo(d->d_halo, (int)d->halo.size(), d->halo_total, d->d_subs,
+                                d->d_step, f == 0 ? -1 : -2, d->dtype, nullptr));
+    GW_TRY_CUDA(cudaDeviceSynchronize());
+    return GW_OK;
+}
+
+gw_status gw_norms(gw_domain *d, double *out, int n)
+{
+    GW_TRY(check_dom(d));
+    if (n < 0 || n > d->step || n > d->shot.cap || (n && !out))
+        return fail(GW_ERR_ARG, "bad norm read (%d of %d steps)", n, d->step);
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    GW_TRY(sync_dom(d));
+    if (n) GW_TRY_CUDA(cudaMemcpy(out, d->d_norms, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    return GW_OK;
+}
+
+gw_status gw_check(gw_domain *d, double *norm2, double *energy)
+{
+    GW_TRY(check_dom(d));
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    GW_TRY(sync_dom(d));
+    GW_TRY_CUDA(cudaMemset(d->d_scratch, 0, 3 * sizeof(double)));
+    for (const SubDev &s : d->subs)
+        GW_TRY_CUDA(launch_check(s, d->step & 1, d->dtype, d->su, d->d_scratch, nullptr));
+    double a[3];
+    GW_TRY_CUDA(cudaMemcpy(a, d->d_scratch, sizeof a, cudaMemcpyDeviceToHost));
+    if (norm2) *norm2 = a[0];
+    if (energy) *energy = a[1] - a[2];
+    if (!std::isfinite(a[0]) || !std::isfinite(a[1]) || !std::isfinite(a[2]))
+        return fail(GW_ERR_NUMERIC, "non-finite check reduction");
+    return GW_OK;
+}
+
+gw_status gw_kernel_timing(gw_domain *d, int enable)
+{
+    GW_TRY(check_dom(d));
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    d->timing = enable != 0;
+    return GW_OK;
+}
+
+gw_status gw_kernel_stats_get(gw_domain *d, gw_kernel_stats *out)
+{
+    GW_TRY(check_dom(d));
+    if (!out) return fail(GW_ERR_ARG, "out is NULL");
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    GW_TRY(sync_dom(d));
+    harvest_events(d);
+    out->launches = d->acc_n;
+    out->total_ms = d->acc_ms;
+    out->halo_ms = d->acc_halo_ms;
+    d->acc_n = 0;
+    d->acc_ms = d->acc_halo_ms = 0;
+    return GW_OK;
+}
+
+gw_status gw_state_bytes(gw_domain *d, size_t *bytes)
+{
+    if (!d || !bytes) return fail(GW_ERR_ARG, "NULL argument");
+    size_t b = 16;
+    const int nf = d->delta ? 3 : 2;
+    for (const SubDev &s : d->subs) {
+        size_t el = (size_t)s.px * s.py * (size_t)(s.nz + 2 * R);
+        b += (size_t)nf * el * d->esize();
+    }
+    *bytes = b;
+    return GW_OK;
+}
+
+static gw_status state_copy(gw_domain *d, char *host, bool save)
+{
+    GW_TRY(check_dom(d));
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    GW_TRY(sync_dom(d));
+    int hdr[4] = {d->step, d->nsub(), d->dtype, 0};
+    if (save) {
+        std::memcpy(host, hdr, sizeof hdr);
+    } else {
+        int got[4];
+        std::memcpy(got, host, sizeof got);
+        if (got[1] != d->nsub() || got[2] != d->dtype)
+            return fail(GW_ERR_ARG, "state does not match this domain");
+        d->step = got[0];
+        GW_TRY_CUDA(cudaMemcpy(d->d_step, &d->step, sizeof(int), cudaMemcpyHostToDevice));
+    }
+    size_t off = 16;
+    const int nf = d->delta ? 3 : 2;
+    for (const SubDev &s : d->subs) {
+        size_t el = (size_t)s.px * s.py * (size_t)(s.nz + 2 * R) * d->esize();
+        char *f[3] = {s.u[0], s.u[1], s.w};
+        for (int i = 0; i < nf; ++i) {
+            if (save)
+                GW_TRY_CUDA(cudaMemcpy(host + off, f[i], el, cudaMemcpyDeviceToHost));
+            else
+                GW_TRY_CUDA(cudaMemcpy(f[i], host + off, el, cudaMemcpyHostToDevice));
+            off += el;
+        }
+    }
+    return GW_OK;
+}
+
+gw_status gw_save_state(gw_domain *d, void *out)
+{
+    if (!out) return fail(GW_ERR_ARG, "out is NULL");
+    return state_copy(d, static_cast<char *>(out), true);
+}
+
+gw_status gw_load_state(gw_domain *d, const void *in)
+{
+    if (!in) return fail(GW_ERR_ARG, "input is NULL");
+    return state_copy(d, const_cast<char *>(static_cast<const char *>(in)), false);
+}
+
+}  // extern "C"

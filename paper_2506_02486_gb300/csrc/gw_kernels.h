@@ -1,0 +1,97 @@
+// gw_kernels.h -- host-side launch interface of the sm_103a kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include "gw_device.h"
+
+namespace gw {
+
+// Storage types (same values as the public GW_* dtype codes).
+enum Dtype { DT_F32 = 0, DT_F64 = 1, DT_F16S = 2, DT_BF16 = 3 };
+
+inline int dtype_size(int dt) { return dt == DT_F64 ? 8 : dt == DT_F32 ? 4 : 2; }
+// Interior x offset in a padded row: >= R and 16-byte aligned.
+inline int dtype_xoff(int dt) { return dtype_size(dt) == 2 ? 8 : 4; }
+
+struct TileInfo {
+    int tx, ty;        // tile extent in x and y (interior points)
+    int threads;       // threads per CTA
+    size_t smem;       // dynamic shared memory bytes
+};
+
+// Tile configurations available for a storage type (ids 0..n-1).
+int step_cfg_count(int dtype);
+bool step_cfg_info(int dtype, int cfg, TileInfo *out);
+// Max resident CTAs per SM of a configuration (after opting in to its
+// shared memory); 0 on error.
+int step_cfg_occupancy(int dtype, int cfg, bool sponge);
+
+// One launch of the fused step kernel over `grid` CTAs.
+cudaError_t launch_step(int dtype, int cfg, bool sponge, int grid,
+                        const StepArgs &a, cudaStream_t s);
+
+// ---- auxiliary kernels (aux_kernels.cu) ----
+
+// Max of n doubles (or floats if f32) into *out (as ordered bits; out must
+// be zero-initialised before the first call of a reduction).
+cudaError_t launch_vmax(const void *v, size_t n, int f32,
+                        unsigned long long *out, cudaStream_t s);
+
+// coef = (v * dt / h)^2 in FP64 for a dense slab of planes [z_lo, z_hi) of
+// a global model, written into the part of subdomain `sub` inside it.
+struct ModelSlab {
+    const void *v;     // dense slab, x fastest, (z_hi - z_lo) planes
+    int f32;           // v is float (else double)
+    int NX, NY;        // global x, y extents
+    int z_lo, z_hi;    // global planes in the slab
+    double dt_over_h;
+};
+cudaError_t launch_coef(const ModelSlab &m, const SubDev &sub, int dtype,
+                        cudaStream_t s);
+
+// Dense <-> padded transfers of a slab of planes of one field.
+// which: 0 = u[cur], 1 = u[cur^1], 2 = w, 3 = coef.  `scale` multiplies on
+// scatter and divides on gather (FP16 scaling).
+struct FieldSlab {
+    void *dense;       // dense slab, x fastest
+    int f64;           // dense is double (else float)
+    int NX, NY;
+    int z_lo, z_hi;
+    int which, cur;
+    double scale;
+};
+cudaError_t launch_scatter(const FieldSlab &f, const SubDev &sub, int dtype,
+                           cudaStream_t s);
+cudaError_t launch_gather(const FieldSlab &f, const SubDev &sub, int dtype,
+                          cudaStream_t s);
+
+// Face-halo copy descriptors: R planes of `src` sub into the halo of `dst`.
+struct HaloDesc {
+    int src, dst;      // subdomain indices
+    int face;          // face of src that is copied (0..5: -x,+x,-y,+y,-z,+z)
+    int pad_;
+    long long first;   // prefix offset of this descriptor's elements
+};
+// Copy all face halos for descriptors [0, ndesc); total = number of
+// elements over all descriptors.  The buffer refreshed is
+// u[(*step + k + 1) & 1]: the new field after step k of the current chunk,
+// or (k = -1) the current field u_n.
+cudaError_t launch_halo(const HaloDesc *descs, int ndesc, long long total,
+                        const SubDev *subs_dev, const int *step, int k,
+                        int dtype, cudaStream_t s);
+
+// End of a chunk of `nk` steps: reduce the per-item norm partials in FP64
+// (fixed order) into each shot's norm log, flag non-finite values, and
+// advance every shot's step counter by nk.
+cudaError_t launch_chunk_end(const ShotDev *shots_dev, int nshots,
+                             const double *partials, int nitems, int nk,
+                             unsigned *err, cudaStream_t s);
+
+// FP64 check reductions over subdomain `sub` of a shot's current state
+// (cur = index of the buffer holding u_n; the other holds u_{n-1}):
+// out[0] += sum u_n^2, out[1] += sum (u_n - u_{n-1})^2 / coef,
+// out[2] += sum u_n lap(u_{n-1}); u unscaled by 1/scale_u.
+cudaError_t launch_check(const SubDev &sub, int cur, int dtype,
+                         double scale_u, double *out, cudaStream_t s);
+
+}  // namespace gw

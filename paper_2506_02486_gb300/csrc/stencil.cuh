@@ -1,0 +1,695 @@
+// stencil.cuh -- the fused Minimod acoustic-isotropic step for sm_103a.
+//
+// One launch advances every subdomain of every shot in the launch by one
+// leapfrog step (8th-order 25-point star Laplacian, Cerjan sponge, point
+// sources, receivers, FP64 norm partials, and -- in fused-halo mode -- the
+// one-sided puts of the new boundary planes into the neighbours' halos,
+// the device-side form of Listing 1's ompx_put; the paper's section 4.5).
+//
+// Work decomposition.  A work item is a tile column: TX x TY points of one
+// subdomain over planes [z0, z1).  Items are ordered z-chunk-major so that
+// the CTAs running at the same time hold neighbouring columns at the same
+// depth (their x/y halo strips are then served from L2), and CTA b takes
+// items b, b + grid, b + 2 grid, ...
+//
+// Per CTA, planes stream through two shared-memory rings filled by TMA
+// (cp.async.bulk.tensor, completion on mbarriers):
+//   * the u ring (SU slots): plane p of u_n with its x/y halo, box
+//     (TX + 2 xoff) x (TY + 8);
+//   * the pointwise ring (SP slots): the TX x TY tiles of the second state
+//     field (u_{n-1}, or w_n for delta storage) and of coef at plane z.
+// Thread 0 issues loads SU - 5 planes ahead of the consumers, across item
+// boundaries.  Each thread owns 4 consecutive x points (one 128-bit group
+// for FP32) of PY rows.  Its z neighbours come from a 9-deep register queue
+// filled from the plane that just arrived (the rotation is compile-time,
+// by unrolling over 9 phases); x/y neighbours come from the staged plane.
+//
+// Arithmetic order (fixed, so that decomposed and undecomposed runs and
+// mirror-image points give identical bits):
+//   s_m = ((u[x-m] + u[x+m]) + (u[y-m] + u[y+m])) + (u[z-m] + u[z+m])
+//   lap = fma(c4, s4, fma(c3, s3, fma(c2, s2, fma(c1, s1, (3 c0) u))))
+//   lap += wavelet[n] at a source cell
+//   3-level: u' = G * fma(coef, lap, fma(-G, u_prev, u + u))
+//   delta:   w' = G * fma(coef, lap, w);  u' = fma(G, u, w')
+// with G = (g_x g_y) g_z from per-axis FP32 tables on global coordinates.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "gw_device.h"
+#include "gw_kernels.h"
+#include "ptx.cuh"
+
+namespace gw {
+
+// ---------------------------------------------------------------- storage
+
+template <class T> struct St;
+
+template <> struct St<float> {
+    using M = float;
+    static constexpr int XO = 4;
+    __device__ static void ld4(const float *p, M v[4])
+    {
+        float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    __device__ static void st4(float *p, const M v[4])
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    __device__ static void st1(float *p, M v) { *p = v; }
+};
+
+template <> struct St<double> {
+    using M = double;
+    static constexpr int XO = 4;
+    __device__ static void ld4(const double *p, M v[4])
+    {
+        double2 a = reinterpret_cast<const double2 *>(p)[0];
+        double2 b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    __device__ static void st4(double *p, const M v[4])
+    {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+    }
+    __device__ static void st1(double *p, M v) { *p = v; }
+};
+
+template <> struct St<__half> {
+    using M = float;
+    static constexpr int XO = 8;
+    __device__ static void ld4(const __half *p, M v[4])
+    {
+        uint2 q = *reinterpret_cast<const uint2 *>(p);
+        float2 a = __half22float2(*reinterpret_cast<__half2 *>(&q.x));
+        float2 b = __half22float2(*reinterpret_cast<__half2 *>(&q.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    __device__ static void st4(__half *p, const M v[4])
+    {
+        __half2 a = __floats2half2_rn(v[0], v[1]);
+        __half2 b = __floats2half2_rn(v[2], v[3]);
+        uint2 q;
+        q.x = *reinterpret_cast<uint32_t *>(&a);
+        q.y = *reinterpret_cast<uint32_t *>(&b);
+        *reinterpret_cast<uint2 *>(p) = q;
+    }
+    __device__ static void st1(__half *p, M v) { *p = __float2half_rn(v); }
+};
+
+template <> struct St<__nv_bfloat16> {
+    using M = float;
+    static constexpr int XO = 8;
+    __device__ static void ld4(const __nv_bfloat16 *p, M v[4])
+    {
+        uint2 q = *reinterpret_cast<const uint2 *>(p);
+        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&q.x));
+        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&q.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    __device__ static void st4(__nv_bfloat16 *p, const M v[4])
+    {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+        __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 q;
+        q.x = *reinterpret_cast<uint32_t *>(&a);
+        q.y = *reinterpret_cast<uint32_t *>(&b);
+        *reinterpret_cast<uint2 *>(p) = q;
+    }
+    __device__ static void st1(__nv_bfloat16 *p, M v)
+    {
+        *p = __float2bfloat16_rn(v);
+    }
+};
+
+// Rounded-once arithmetic in the math type (no contraction by the compiler).
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// 8th-order central second-difference weights (Taylor table), with the
+// centre weight already multiplied by 3 for the three axes.
+template <class M> struct W {
+    static constexpr M c0x3 = M(-615.0 / 72.0);
+    static constexpr M c1 = M(8.0 / 5.0);
+    static constexpr M c2 = M(-1.0 / 5.0);
+    static constexpr M c3 = M(8.0 / 315.0);
+    static constexpr M c4 = M(-1.0 / 560.0);
+};
+
+// ---------------------------------------------------------------- config
+
+template <class T_, int TX_, int TY_, int PY_, int SU_, int SP_>
+struct Cfg {
+    using T = T_;
+    using M = typename St<T>::M;
+    // coefficient storage: FP16 next to 16-bit wavefields, else T
+    using CT = typename std::conditional<sizeof(T_) == 2, __half, T_>::type;
+    static constexpr int TX = TX_, TY = TY_, PY = PY_, SU = SU_, SP = SP_;
+    static constexpr int NTX = TX / 4, NTY = TY / PY, NT = NTX * NTY;
+    static constexpr int XO = St<T>::XO;
+    static constexpr int RW = TX + 2 * XO;          // smem row (elements)
+    static constexpr int UROWS = TY + 2 * R;
+    static constexpr int UBYTES = RW * UROWS * (int)sizeof(T);
+    static constexpr int PBYTES = TX * TY * (int)sizeof(T);
+    static constexpr int OFF_P = SU * UBYTES;
+    static constexpr int OFF_BAR = OFF_P + SP * 2 * PBYTES;
+    static constexpr int OFF_LOC = OFF_BAR + 8 * (SU + SP);
+    static constexpr int OFF_MISC = OFF_LOC + 16 * kMaxLocal;
+    static constexpr int OFF_RED = OFF_MISC + 16;
+    static constexpr int SMEM = OFF_RED + 8 * (NT / 32);
+    static_assert(TX % 4 == 0 && TY % PY == 0 && NT % 32 == 0, "tile");
+    static_assert(UBYTES % 128 == 0 && PBYTES % 128 == 0, "TMA alignment");
+    static_assert((RW * (int)sizeof(T)) % 16 == 0, "TMA box row");
+    static_assert(SU >= 6 && SP >= 2, "ring depth");
+};
+
+// ---------------------------------------------------------------- kernel
+
+template <class C, bool DELTA, bool SPONGE>
+struct Step {
+    using T = typename C::T;
+    using M = typename C::M;
+    using S = St<T>;
+    static constexpr int TX = C::TX, TY = C::TY, PY = C::PY;
+    static constexpr int SU = C::SU, SP = C::SP, XO = C::XO;
+
+    const StepArgs &A;
+    unsigned char *smem;
+    int tid, tx, ty;
+
+    // producer (thread 0)
+    int lp_it, lp_t, lp_T, lp_x, lp_y, lp_z;
+    const char *lp_map;
+    int pp_it, pp_j, pp_J, pp_x, pp_y, pp_z;
+    const char *pp_map_a, *pp_map_b;
+    unsigned l_issued, p_issued;
+    uint64_t pol_first, pol_last;
+
+    // consumer
+    unsigned tg, jg;           // u loads / pointwise planes consumed
+    bool aborted;              // this thread's wait gave up
+    bool cta_abort;            // some thread's wait gave up (CTA-uniform)
+
+    // current item
+    int sub, x0, y0, z0, z1, n, par;
+    int nx, ny, nz;
+    int vx;                    // valid x points of this thread (0..4)
+    bool rowok[PY];
+    const SubDev *sd;
+    const ShotDev *sh;
+    T *unext, *wbuf;
+    M gxy[PY][4];
+    M acc;
+    M Q[9][PY][4];
+
+    __device__ Step(const StepArgs &a, unsigned char *sm) : A(a), smem(sm) {}
+
+    __device__ T *ubuf(unsigned slot)
+    {
+        return reinterpret_cast<T *>(smem + slot * C::UBYTES);
+    }
+    __device__ T *pbuf(unsigned slot, int f)
+    {
+        return reinterpret_cast<T *>(smem + C::OFF_P +
+                                     (slot * 2 + f) * C::PBYTES);
+    }
+    __device__ uint64_t *ufull(unsigned slot)
+    {
+        return reinterpret_cast<uint64_t *>(smem + C::OFF_BAR) + slot;
+    }
+    __device__ uint64_t *pfull(unsigned slot)
+    {
+        return reinterpret_cast<uint64_t *>(smem + C::OFF_BAR) + SU + slot;
+    }
+    __device__ int4 *loc() { return reinterpret_cast<int4 *>(smem + C::OFF_LOC); }
+    __device__ int *misc() { return reinterpret_cast<int *>(smem + C::OFF_MISC); }
+    __device__ double *red() { return reinterpret_cast<double *>(smem + C::OFF_RED); }
+
+    __device__ int step_of(const Item &I) const
+    {
+        const SubDev &s = A.subs[I.sub];
+        return *A.shots[s.shot].step + A.k;
+    }
+
+    // ---- producer -----------------------------------------------------
+    __device__ void lp_decode()
+    {
+        if (lp_it >= A.nitems) return;
+        Item I = A.items[lp_it];
+        int p = step_of(I) & 1;
+        lp_map = static_cast<const char *>(A.maps) +
+                 (size_t)(I.sub * kMapsPerSub + (p ? MAP_U1_HALO : MAP_U0_HALO)) * 128;
+        lp_x = I.xy & 0xffff;          // padded x of interior x0 - XO
+        lp_y = I.xy >> 16;             // padded y of interior y0 - R
+        lp_z = I.z0;                   // padded z of interior z0 - R
+        lp_T = I.z1 - I.z0 + 2 * R;
+        lp_t = 0;
+        tensormap_acquire(lp_map);
+    }
+    __device__ void pp_decode()
+    {
+        if (pp_it >= A.nitems) return;
+        Item I = A.items[pp_it];
+        int p = step_of(I) & 1;
+        const char *base = static_cast<const char *>(A.maps) +
+                           (size_t)I.sub * kMapsPerSub * 128;
+        int slot_a = DELTA ? MAP_W_PW : (p ? MAP_U0_PW : MAP_U1_PW);
+        pp_map_a = base + slot_a * 128;
+        pp_map_b = base + MAP_COEF_PW * 128;
+        pp_x = (I.xy & 0xffff) + XO;
+        pp_y = (I.xy >> 16) + R;
+        pp_z = I.z0 + R;
+        pp_J = I.z1 - I.z0;
+        pp_j = 0;
+        tensormap_acquire(pp_map_a);
+        tensormap_acquire(pp_map_b);
+    }
+    __device__ void issue_u()
+    {
+        if (lp_it >= A.nitems) return;
+        unsigned slot = l_issued % SU;
+        uint64_t *bar = ufull(slot);
+        mbar_arrive_expect_tx(bar, C::UBYTES);
+        tma_load_3d(ubuf(slot), lp_map, bar, lp_x, lp_y, lp_z + lp_t, pol_last);
+        ++l_issued;
+        if (++lp_t == lp_T) {
+            lp_it += gridDim.x;
+            lp_decode();
+        }
+    }
+    __device__ void issue_p()
+    {
+        if (pp_it >= A.nitems) return;
+        unsigned slot = p_issued % SP;
+        uint64_t *bar = pfull(slot);
+        mbar_arrive_expect_tx(bar, 2 * C::PBYTES);
+        tma_load_3d(pbuf(slot, 0), pp_map_a, bar, pp_x, pp_y, pp_z + pp_j, pol_first);
+        tma_load_3d(pbuf(slot, 1), pp_map_b, bar, pp_x, pp_y, pp_z + pp_j, pol_first);
+        ++p_issued;
+        if (++pp_j == pp_J) {
+            pp_it += gridDim.x;
+            pp_decode();
+        }
+    }
+
+    __device__ void wait_or_abort(uint64_t *bar, uint32_t parity)
+    {
+        if (!mbar_wait(bar, parity)) {
+            atomicOr(A.err, ERRB_TIMEOUT);
+            aborted = true;
+        }
+    }
+
+    // ---- item set-up ----------------------------------------------------
+    __device__ void begin_item(int it)
+    {
+        Item I = A.items[it];
+        sub = I.sub;
+        sd = &A.subs[sub];
+        sh = &A.shots[sd->shot];
+        x0 = I.xy & 0xffff;
+        y0 = I.xy >> 16;
+        z0 = I.z0;
+        z1 = I.z1;
+        nx = sd->nx; ny = sd->ny; nz = sd->nz;
+        n = *sh->step + A.k;
+        par = n & 1;
+        unext = reinterpret_cast<T *>(sd->u[par ^ 1]);
+        wbuf = reinterpret_cast<T *>(sd->w);
+        int xs = x0 + 4 * tx;
+        vx = min(4, max(0, nx - xs));
+#pragma unroll
+        for (int r = 0; r < PY; ++r) rowok[r] = (y0 + PY * ty + r) < ny;
+        if (SPONGE) {
+#pragma unroll
+            for (int r = 0; r < PY; ++r) {
+                int gy = min(sd->gy0 + y0 + PY * ty + r, sh->NY - 1);
+                M fy = (M)__ldg(sh->gy + gy);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    int gx = min(sd->gx0 + xs + i, sh->NX - 1);
+                    gxy[r][i] = mul_rn((M)__ldg(sh->gx + gx), fy);
+                }
+            }
+        }
+        acc = M(0);
+        // receivers and sources inside this item -> shared list (warp 0)
+        if (tid < 32) {
+            int cnt = 0;
+            int lane = tid;
+            int gxa = sd->gx0 + x0, gya = sd->gy0 + y0, gza = sd->gz0;
+            int xl_end = min(TX, nx - x0), yl_end = min(TY, ny - y0);
+            for (int pass = 0; pass < 2; ++pass) {
+                int nlist = pass == 0 ? sh->nsrc : sh->nrec;
+                const int4 *list = pass == 0 ? sh->src : sh->rec;
+                for (int b = 0; b < nlist; b += 32) {
+                    int e = b + lane;
+                    bool in = false;
+                    int4 q = make_int4(0, 0, 0, 0);
+                    if (e < nlist) {
+                        int4 g = list[e];
+                        int lx = g.x - gxa, ly = g.y - gya, lz = g.z - gza;
+                        in = lx >= 0 && lx < xl_end && ly >= 0 && ly < yl_end &&
+                             lz >= z0 && lz < z1;
+                        q = make_int4(pass == 0 ? -1 - e : e, lx | (ly << 16), lz, 0);
+                    }
+                    unsigned m = __ballot_sync(0xffffffffu, in);
+                    int pos = cnt + __popc(m & ((1u << lane) - 1u));
+                    if (in) {
+                        if (pos < kMaxLocal) loc()[pos] = q;
+                        else atomicOr(A.err, ERRB_LOCAL_OVERFLOW);
+                    }
+                    cnt += __popc(m);
+                }
+            }
+            if (lane == 0) misc()[0] = min(cnt, kMaxLocal);
+        }
+    }
+
+    __device__ void end_item(int it)
+    {
+        double v = (double)acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red()[tid >> 5] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int w = 0; w < C::NT / 32; ++w) s += red()[w];
+            A.partials[(size_t)A.k * A.nitems + it] = s;
+        }
+    }
+
+    // ---- one u-plane iteration -----------------------------------------
+    // Phase PH = t mod 9 fixes where plane t lands in the register queue.
+    template <int PH>
+    __device__ __forceinline__ void iter(int t)
+    {
+        if (cta_abort) return;   // a wait gave up: leave uniformly
+        // (1) the plane of load t: append its centre values to the queue
+        {
+            unsigned slot = tg % SU;
+            wait_or_abort(ufull(slot), (tg / SU) & 1u);
+            const T *pl = ubuf(slot);
+#pragma unroll
+            for (int r = 0; r < PY; ++r)
+                S::ld4(pl + (PY * ty + r + R) * C::RW + XO + 4 * tx, Q[PH][r]);
+        }
+        // (2) compute plane z = z0 + t - 8 once the queue is full
+        if (t >= 2 * R) {
+            const int z = z0 + t - 2 * R;
+            const T *pl = ubuf((tg - R) % SU);
+            unsigned ps = jg % SP;
+            wait_or_abort(pfull(ps), (jg / SP) & 1u);
+            M yv[PY + 8][4];
+#pragma unroll
+            for (int j = 0; j < PY + 8; ++j)
+                S::ld4(pl + (PY * ty + j) * C::RW + XO + 4 * tx, yv[j]);
+            M lf[PY][4], rt[PY][4], pa[PY][4], cf[PY][4];
+#pragma unroll
+            for (int r = 0; r < PY; ++r) {
+                const T *row = pl + (PY * ty + r + R) * C::RW + XO + 4 * tx;
+                S::ld4(row - 4, lf[r]);
+                S::ld4(row + 4, rt[r]);
+                S::ld4(pbuf(ps, 0) + (PY * ty + r) * TX + 4 * tx, pa[r]);
+                St<typename C::CT>::ld4(
+                    reinterpret_cast<const typename C::CT *>(pbuf(ps, 1)) +
+                        (PY * ty + r) * TX + 4 * tx, cf[r]);
+            }
+            M gz = M(1);
+            if (SPONGE) gz = (M)__ldg(sh->gz + sd->gz0 + z);
+
+            M lap[PY][4];
+#pragma unroll
+            for (int r = 0; r < PY; ++r) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    M s[5];
+#pragma unroll
+                    for (int m = 1; m <= 4; ++m) {
+                        M xm = (i - m >= 0) ? yv[r + R][i - m] : lf[r][4 + i - m];
+                        M xp = (i + m <= 3) ? yv[r + R][i + m] : rt[r][i + m - 4];
+                        M ym = yv[r + R - m][i];
+                        M yp = yv[r + R + m][i];
+                        M zm = Q[(PH + 9 - R - m) % 9][r][i];
+                        M zp = Q[(PH + 9 - R + m) % 9][r][i];
+                        s[m] = add_rn(add_rn(add_rn(xm, xp), add_rn(ym, yp)),
+                                      add_rn(zm, zp));
+                    }
+                    M c = yv[r + R][i];
+                    M l = fma_rn(W<M>::c1, s[1], mul_rn(W<M>::c0x3, c));
+                    l = fma_rn(W<M>::c2, s[2], l);
+                    l = fma_rn(W<M>::c3, s[3], l);
+                    l = fma_rn(W<M>::c4, s[4], l);
+                    // delta storage holds su * u: undo the power-of-two scale
+                    if (DELTA) l = mul_rn(l, (M)sh->isu);
+                    lap[r][i] = l;
+                }
+            }
+            const int nl = misc()[0];
+            // point sources: lap += wavelet[n] at the source cell
+            for (int e = 0; e < nl; ++e) {
+                int4 q = loc()[e];
+                if (q.x < 0 && q.z == z) {
+                    int lx = q.y & 0xffff, ly = q.y >> 16;
+                    if ((lx >> 2) == tx && ly / PY == ty && n < sh->cap) {
+                        M wv = (M)__ldg(sh->wavelet + (size_t)(-1 - q.x) * sh->cap + n);
+#pragma unroll
+                        for (int r = 0; r < PY; ++r)
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                if (r == ly % PY && i == (lx & 3))
+                                    lap[r][i] = add_rn(lap[r][i], wv);
+                    }
+                }
+            }
+            // leapfrog update with the sponge
+            M un[PY][4], wn[PY][4];
+#pragma unroll
+            for (int r = 0; r < PY; ++r) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    M G = SPONGE ? mul_rn(gxy[r][i], gz) : M(1);
+                    M u = yv[r + R][i];
+                    if (DELTA) {
+                        M w = mul_rn(pa[r][i], (M)sh->isw);
+                        M uu = mul_rn(u, (M)sh->isu);
+                        M a = fma_rn(cf[r][i], lap[r][i], w);
+                        wn[r][i] = SPONGE ? mul_rn(G, a) : a;
+                        un[r][i] = SPONGE ? fma_rn(G, uu, wn[r][i])
+                                          : add_rn(uu, wn[r][i]);
+                    } else {
+                        M tt = SPONGE ? fma_rn(-G, pa[r][i], add_rn(u, u))
+                                      : add_rn(add_rn(u, u), -pa[r][i]);
+                        M a = fma_rn(cf[r][i], lap[r][i], tt);
+                        un[r][i] = SPONGE ? mul_rn(G, a) : a;
+                    }
+                }
+            }
+            // stores: u' (and w') at this plane; norm partial
+            const size_t plane = (size_t)sd->px * sd->py;
+#pragma unroll
+            for (int r = 0; r < PY; ++r) {
+                if (!rowok[r] || vx == 0) continue;
+                const int y = y0 + PY * ty + r;
+                const int x = x0 + 4 * tx;
+                const size_t off = (size_t)(z + R) * plane +
+                                   (size_t)(y + R) * sd->px + XO + x;
+                M so[4], sw[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    so[i] = DELTA ? mul_rn(un[r][i], (M)sh->su) : un[r][i];
+                    sw[i] = DELTA ? mul_rn(wn[r][i], (M)sh->sw) : M(0);
+                    if (i < vx) acc = fma_rn(un[r][i], un[r][i], acc);
+                }
+                if (vx == 4) {
+                    S::st4(unext + off, so);
+                    if (DELTA) S::st4(wbuf + off, sw);
+                } else {
+                    for (int i = 0; i < vx; ++i) {
+                        S::st1(unext + off + i, so[i]);
+                        if (DELTA) S::st1(wbuf + off + i, sw[i]);
+                    }
+                }
+                if (A.fused_halo) put_halo_row(x, y, z, so);
+            }
+            // receivers: trace[n] = u_{n+1}
+            for (int e = 0; e < nl; ++e) {
+                int4 q = loc()[e];
+                if (q.x >= 0 && q.z == z) {
+                    int lx = q.y & 0xffff, ly = q.y >> 16;
+                    if ((lx >> 2) == tx && ly / PY == ty && n < sh->cap) {
+                        M v = M(0);
+#pragma unroll
+                        for (int r = 0; r < PY; ++r)
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                if (r == ly % PY && i == (lx & 3)) v = un[r][i];
+                        sh->traces[(size_t)q.x * sh->cap + n] = (float)v;
+                    }
+                }
+            }
+            ++jg;
+        }
+        ++tg;
+        // the barrier also votes: every thread learns whether any wait gave up
+        cta_abort = __syncthreads_or(aborted) != 0;
+        if (tid == 0 && !cta_abort) {
+            issue_u();
+            if (t >= 2 * R) issue_p();
+        }
+    }
+
+    // One-sided puts of a freshly computed row segment into the halos of
+    // the face neighbours that read it (Listing 1's ompx_put, fused).
+    __device__ void put_row(int nb, int x, int y, int z, const M so[4],
+                            int ncount, bool vec)
+    {
+        const SubDev &o = A.subs[nb];
+        T *base;
+        if (A.symmetric)
+            base = reinterpret_cast<T *>(
+                reinterpret_cast<char *>(unext) +
+                (long long)(o.rank - sd->rank) * A.rank_stride);
+        else
+            base = reinterpret_cast<T *>(o.u[par ^ 1]);
+        const size_t off = ((size_t)(z + R) * o.py + (size_t)(y + R)) * o.px + XO + x;
+        if (vec) {
+            S::st4(base + off, so);
+        } else {
+            for (int i = 0; i < ncount; ++i) S::st1(base + off + i, so[i]);
+        }
+    }
+
+    __device__ void put_halo_row(int x, int y, int z, const M so[4])
+    {
+        const int *nb = sd->nbr;
+        const bool vec = vx == 4;
+        if (z < R && nb[4] >= 0)
+            put_row(nb[4], x, y, A.subs[nb[4]].nz + z, so, vx, vec);
+        if (z >= nz - R && nb[5] >= 0)
+            put_row(nb[5], x, y, z - nz, so, vx, vec);
+        if (y < R && nb[2] >= 0)
+            put_row(nb[2], x, A.subs[nb[2]].ny + y, z, so, vx, vec);
+        if (y >= ny - R && nb[3] >= 0)
+            put_row(nb[3], x, y - ny, z, so, vx, vec);
+        if (x < R && nb[0] >= 0) {
+            const int onx = A.subs[nb[0]].nx;
+            for (int i = 0; i < vx; ++i)
+                if (x + i < R) put_row(nb[0], onx + x + i, y, z, so + i, 1, false);
+        }
+        if (x + vx > nx - R && nb[1] >= 0) {
+            for (int i = 0; i < vx; ++i)
+                if (x + i >= nx - R) put_row(nb[1], x + i - nx, y, z, so + i, 1, false);
+        }
+    }
+
+    __device__ void run()
+    {
+        tid = threadIdx.x;
+        tx = tid % C::NTX;
+        ty = tid / C::NTX;
+        aborted = false;
+        cta_abort = false;
+        tg = jg = 0;
+        if (tid == 0) {
+            for (int s = 0; s < SU; ++s) mbar_init(ufull(s), 1);
+            for (int s = 0; s < SP; ++s) mbar_init(pfull(s), 1);
+            fence_barrier_init();
+        }
+        __syncthreads();
+        if (tid == 0) {
+            pol_first = policy_evict_first();
+            pol_last = policy_evict_last();
+            l_issued = p_issued = 0;
+            lp_it = pp_it = blockIdx.x;
+            lp_decode();
+            pp_decode();
+            for (int i = 0; i < SU - 4; ++i) issue_u();
+            for (int i = 0; i < SP; ++i) issue_p();
+        }
+        for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
+            begin_item(it);
+            const int T = z1 - z0 + 2 * R;
+            for (int tb = 0; tb < T; tb += 9) {
+                iter<0>(tb);
+                if (tb + 1 < T) iter<1>(tb + 1);
+                if (tb + 2 < T) iter<2>(tb + 2);
+                if (tb + 3 < T) iter<3>(tb + 3);
+                if (tb + 4 < T) iter<4>(tb + 4);
+                if (tb + 5 < T) iter<5>(tb + 5);
+                if (tb + 6 < T) iter<6>(tb + 6);
+                if (tb + 7 < T) iter<7>(tb + 7);
+                if (tb + 8 < T) iter<8>(tb + 8);
+                if (cta_abort) break;
+            }
+            if (cta_abort) break;
+            end_item(it);
+        }
+        // drain: wait (bounded) for every load still in flight
+        if (tid == 0) {
+            for (unsigned q = tg; q < l_issued; ++q)
+                if (!mbar_wait(ufull(q % SU), (q / SU) & 1u)) break;
+            for (unsigned q = jg; q < p_issued; ++q)
+                if (!mbar_wait(pfull(q % SP), (q / SP) & 1u)) break;
+        }
+    }
+};
+
+template <class C, bool DELTA, bool SPONGE>
+__global__ void __launch_bounds__(C::NT, 1)
+k_step(const __grid_constant__ StepArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    Step<C, DELTA, SPONGE> s(a, smem);
+    s.run();
+}
+
+template <class C>
+static TileInfo info_of()
+{
+    return TileInfo{C::TX, C::TY, C::NT, (size_t)C::SMEM};
+}
+
+template <class C, bool DELTA>
+static cudaError_t launch_cfg(bool sponge, int grid, const StepArgs &a,
+                              cudaStream_t s)
+{
+    auto kern = sponge ? k_step<C, DELTA, true> : k_step<C, DELTA, false>;
+    static bool attr_done[2] = {false, false};
+    if (!attr_done[sponge]) {
+        cudaError_t e = cudaFuncSetAttribute(
+            kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_done[sponge] = true;
+    }
+    kern<<<grid, C::NT, C::SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class C, bool DELTA>
+static int occ_cfg(bool sponge)
+{
+    auto kern = sponge ? k_step<C, DELTA, true> : k_step<C, DELTA, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             C::SMEM) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, C::NT,
+                                                      C::SMEM) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+}  // namespace gw

@@ -1,0 +1,67 @@
+// stencil_dispatch.cpp -- (storage type, tile id) -> the step-kernel
+// instantiation compiled from stencil_inst.cu with -DGW_INST=<index>.
+#include "gw_kernels.h"
+
+namespace gw {
+
+#define GW_DECL(I)                                                          \
+    cudaError_t step_launch_##I(bool, int, const StepArgs &, cudaStream_t); \
+    int step_occ_##I(bool);                                                 \
+    TileInfo step_info_##I();
+GW_DECL(0) GW_DECL(1) GW_DECL(2) GW_DECL(3) GW_DECL(4) GW_DECL(5)
+GW_DECL(6) GW_DECL(7) GW_DECL(8) GW_DECL(9) GW_DECL(10) GW_DECL(11)
+#undef GW_DECL
+
+namespace {
+struct Entry {
+    int dtype, id;
+    cudaError_t (*launch)(bool, int, const StepArgs &, cudaStream_t);
+    int (*occ)(bool);
+    TileInfo (*info)();
+};
+#define GW_E(I, D, ID) {D, ID, step_launch_##I, step_occ_##I, step_info_##I}
+const Entry kTable[] = {
+    GW_E(0, DT_F32, 0),  GW_E(1, DT_F32, 1),   GW_E(2, DT_F32, 2),
+    GW_E(3, DT_F32, 3),  GW_E(4, DT_F64, 0),   GW_E(5, DT_F64, 1),
+    GW_E(6, DT_F16S, 0), GW_E(7, DT_F16S, 1),  GW_E(8, DT_F16S, 2),
+    GW_E(9, DT_BF16, 0), GW_E(10, DT_BF16, 1), GW_E(11, DT_BF16, 2),
+};
+#undef GW_E
+
+const Entry *find(int dtype, int id)
+{
+    for (const Entry &e : kTable)
+        if (e.dtype == dtype && e.id == id) return &e;
+    return nullptr;
+}
+}  // namespace
+
+int step_cfg_count(int dtype)
+{
+    int n = 0;
+    for (const Entry &e : kTable) n += e.dtype == dtype;
+    return n;
+}
+
+bool step_cfg_info(int dtype, int cfg, TileInfo *out)
+{
+    const Entry *e = find(dtype, cfg);
+    if (!e) return false;
+    *out = e->info();
+    return true;
+}
+
+int step_cfg_occupancy(int dtype, int cfg, bool sponge)
+{
+    const Entry *e = find(dtype, cfg);
+    return e ? e->occ(sponge) : 0;
+}
+
+cudaError_t launch_step(int dtype, int cfg, bool sponge, int grid,
+                        const StepArgs &a, cudaStream_t s)
+{
+    const Entry *e = find(dtype, cfg);
+    return e ? e->launch(sponge, grid, a, s) : cudaErrorInvalidValue;
+}
+
+}  // namespace gw

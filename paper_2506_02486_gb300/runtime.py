@@ -1,0 +1,130 @@
+"""PyTorch-owned global segment and a one-shot helper over the C ABI.
+
+PyTorch only provides the device memory (one ``uint8`` tensor that becomes
+the PGAS global segment, paper section 3.2) and streams; every step of the
+computation runs in the library's kernels.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from . import gbwave as gw
+
+
+class Segment:
+    """A device buffer attached as the global segment of a new context."""
+
+    def __init__(self, nbytes: int, nranks: int = 1, device: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the gbwave library needs a CUDA device")
+        self.device = device
+        self.nbytes = int(nbytes)
+        self.nranks = int(nranks)
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8,
+                               device=f"cuda:{device}")
+        self.ctx = gw.gw_ctx_create(device)
+        gw.gw_segment_attach(self.ctx, self.buf, self.nbytes, self.nranks)
+
+    def close(self):
+        if self.ctx:
+            gw.gw_ctx_destroy(self.ctx)
+            self.ctx = 0
+        self.buf = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def padded_bytes(nx: int, ny: int, nz: int, dtype: str = "f32") -> int:
+    """Bytes of one padded field array (x pitch a multiple of 128 bytes)."""
+    es = {"f32": 4, "f64": 8, "f16s": 2, "bf16": 2}[dtype]
+    xo = 8 if es == 2 else 4
+    mul = 128 // es
+    px = -(-(xo + nx + 4) // mul) * mul
+    return px * (ny + 8) * (nz + 8) * es
+
+
+def shot_bytes(nx: int, ny: int, nz: int, dtype: str = "f32",
+               nsteps: int = 1, nrec: int = 0, px=1, py=1, pz=1) -> int:
+    """A generous segment size for one shot (fields + metadata + staging)."""
+    nsub = px * py * pz
+    sx, sy, sz = -(-nx // px), -(-ny // py), -(-nz // pz)
+    f = padded_bytes(sx, sy, sz, dtype)
+    nfields = 4 if dtype in ("f16s", "bf16") else 3
+    meta = 64 << 20
+    stage = min(256 << 20, nx * ny * nz * 8) + (1 << 20)
+    items = (nx // 16 + 1) * (ny // 8 + 1) * 64 * 8 * 32
+    return nsub * (nfields * f + (4 << 20)) + meta + stage + items \
+        + nrec * nsteps * 4
+
+
+class Shot:
+    """One shot domain with its model, source and receivers."""
+
+    def __init__(self, seg: Segment, nx, ny, nz, *, px=1, py=1, pz=1,
+                 split=(None, None, None), symmetric=True, **desc):
+        self.seg = seg
+        self.shape = (nz, ny, nx)
+        self.desc = gw.shot_desc(nx, ny, nz, **desc)
+        self.dom = gw.gw_domain_create(seg.ctx, self.desc, px, py, pz,
+                                       split[0], split[1], split[2],
+                                       symmetric)
+        self.nrec = 0
+
+    @property
+    def info(self) -> dict:
+        return gw.gw_domain_info_get(self.dom)
+
+    def set_model(self, vel: np.ndarray):
+        gw.gw_set_model(self.dom, vel)
+
+    def add_ricker(self, pos, f_peak: float, nsteps: int | None = None):
+        n = self.desc.nsteps if nsteps is None else nsteps
+        w = gw.gw_ricker(f_peak, self.info["dt"], n)
+        gw.gw_inject_source(self.dom, *pos, w)
+        return w
+
+    def add_source(self, pos, wavelet):
+        gw.gw_inject_source(self.dom, *pos, wavelet)
+
+    def set_receivers(self, xyz):
+        xyz = np.asarray(xyz, dtype=np.int32).reshape(-1, 3)
+        gw.gw_set_receivers(self.dom, xyz)
+        self.nrec = xyz.shape[0]
+
+    def step(self, n: int, stream=None):
+        gw.gw_step(self.dom, n, stream)
+
+    def sync(self):
+        gw.gw_barrier(self.dom, None, True)
+
+    def u(self, which=gw.GW_FIELD_U, f64=True) -> np.ndarray:
+        return gw.gw_read_wavefield(self.dom, which, self.shape, f64)
+
+    def write(self, which, arr):
+        gw.gw_write_wavefield(self.dom, which, arr)
+
+    def traces(self, nsteps: int) -> np.ndarray:
+        return gw.gw_read_receivers(self.dom, self.nrec, nsteps)
+
+    def norms(self, n: int) -> np.ndarray:
+        return gw.gw_norms(self.dom, n)
+
+    def check(self) -> tuple[float, float]:
+        return gw.gw_check(self.dom)
+
+    def close(self):
+        if self.dom:
+            gw.gw_domain_destroy(self.dom)
+            self.dom = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -191,3 +191,53 @@ def arrival_stream(seed: int, n: int = 2000, rate_per_s: float = 10.0,
                               side, side, nz, margin=sponge)
         out.append(Request(t, side, side, nz, steps, dt, mseed, src, sponge))
     return out
+
+
+@dataclass
+class ShotInputs:
+    """Everything a single-shot run draws: model, source, receivers."""
+    name: str
+    vel: np.ndarray
+    src: tuple[int, int, int]
+    receivers: np.ndarray
+    f_peak: float
+    nsteps: int
+    sponge: int
+    h: float = 10.0
+
+
+def plain_cube(n: int = 64, nsteps: int = 100) -> ShotInputs:
+    """Homogeneous 1500 m/s cube, 15 Hz source at interior index n/2 in
+    every axis, no sponge (zero halo only), receivers on the source line."""
+    vel = homogeneous(n, n, n, 1500.0)
+    c = n // 2
+    rec = np.array([[c, c, c], [c // 3, c, c], [c, c, n - 1 - c // 4]],
+                   dtype=np.int32)
+    return ShotInputs(f"plain_{n}cubed", vel, (c, c, c), rec, 15.0, nsteps, 0)
+
+
+def layered_cube(n: int = 512, seed: int = 2506, nsteps: int = 1000,
+                 sponge: int = 20) -> ShotInputs:
+    """8-layer model (1500-4500 m/s) on an n^3 grid, 20-cell sponge, 20 Hz
+    source at a seeded cell outside the sponge, 8 x 8 receivers on the
+    first plane below the top sponge."""
+    vel = layered(n, n, n, seed)
+    src = source_position(seed + 1, n, n, n, margin=sponge)
+    rec = lattice_receivers(n, n, sponge, n=8, margin=sponge)
+    return ShotInputs(f"layered_{n}cubed", vel, src, rec, 20.0, nsteps,
+                      sponge)
+
+
+def perturbed_box(nx: int = 1024, ny: int = 1024, nz: int = 512,
+                  seed: int = 2507, nsteps: int = 500, sponge: int = 20,
+                  vel_dtype=np.float32) -> ShotInputs:
+    """The layered model with 5% i.i.d. Gaussian perturbations (clipped at
+    20%) on an nx x ny x nz grid; 20 Hz source at a seeded cell."""
+    base = np.empty((nz, ny, nx), dtype=vel_dtype)
+    rng = np.random.default_rng(seed)
+    base[...] = _layer_profile(nz, rng, 8, 1500.0, 4500.0)[:, None, None]
+    vel = perturbed(base, seed + 1, out_dtype=vel_dtype)
+    src = source_position(seed + 2, nx, ny, nz, margin=sponge)
+    rec = lattice_receivers(nx, ny, sponge, n=8, margin=sponge)
+    return ShotInputs(f"perturbed_{nx}x{ny}x{nz}", vel, src, rec, 20.0,
+                      nsteps, sponge)
