@@ -318,16 +318,14 @@ def run_e2e(seg, shot, steps):
     dom = gw.gw_domain_create(seg.ctx, desc)
     try:
         gw.gw_set_model(dom, vel_pinned.numpy())
-        dt = gw.gw_domain_info_get(dom)["dt"]
-        wl = gw.gw_ricker(shot.f_peak, dt, steps)
-        gw.gw_inject_source(dom, *shot.src, wl)
+        gw.gw_inject_ricker(dom, *shot.src, shot.f_peak)
         gw.gw_set_receivers(dom, rec)
         gw.gw_step(dom, steps, torch.cuda.current_stream())
         gw.gw_read_receivers(dom, rec.shape[0], steps, out=traces.numpy())
     finally:
         gw.gw_domain_destroy(dom)
     el = time.perf_counter() - t
-    h2d = shot.vel.nbytes + wl.nbytes + rec.nbytes
+    h2d = shot.vel.nbytes + rec.nbytes
     d2h = traces.numel() * 4
     return el, h2d, d2h
 

@@ -229,9 +229,16 @@ gw_status gw_ricker(double f_peak, double dt, int n, float *out);
 
 /* Add a point source at global interior cell (gx, gy, gz) with wavelet
  * samples wavelet[0..n) (FP32 host; sample n is added to lap(u_n) when
- * computing u_{n+1}; steps beyond n add nothing).  Up to 16 sources. */
+ * computing u_{n+1}; steps beyond n add nothing).  Up to 16 sources.
+ * Samples are kept in FP64 and rounded to the arithmetic type in the
+ * kernel. */
 gw_status gw_inject_source(gw_domain *d, int gx, int gy, int gz,
                            const float *wavelet, int n);
+/* The same with the library's own Ricker wavelet of peak frequency f_peak
+ * (Hz), sampled in FP64 at t_n = n dt with the delay 1/f_peak (the
+ * formula of gw_ricker), for n < desc.nsteps.  Needs the model (dt). */
+gw_status gw_inject_ricker(gw_domain *d, int gx, int gy, int gz,
+                           double f_peak);
 /* Receivers: nrec (x, y, z) global interior cells; trace sample n is
  * u_{n+1} at the receiver, for n < desc.nsteps.  Replaces earlier ones. */
 gw_status gw_set_receivers(gw_domain *d, int nrec, const int *xyz);

@@ -87,9 +87,9 @@ struct gw_domain {
     unsigned *d_err = nullptr;
     int *d_step = nullptr;
     double *d_scratch = nullptr;          // 4 doubles for checks
-    float *d_wavelet = nullptr;
+    double *d_wavelet = nullptr;
     double *d_norms = nullptr;
-    float *d_gtab = nullptr;              // gx | gy | gz
+    double *d_gtab = nullptr;             // gx | gy | gz
     int4 *d_src = nullptr;
     int4 *d_rec = nullptr;
     float *d_traces = nullptr;
@@ -107,6 +107,7 @@ struct gw_domain {
     long long halo_total = 0;
     // sources and receivers (host copies)
     std::vector<int4> srcs;
+    std::vector<std::vector<double>> wavelets;
     int nrec = 0;
     // model
     double dt = 0, vmax = 0, courant = 0;
@@ -619,9 +620,9 @@ gw_status gw_domain_create(gw_ctx *c, const gw_shot_desc *desc, int px, int py,
     size_t off_step = off_err + 64;
     size_t off_scr = off_err + 128;
     size_t off_wl = align_up(off_scr + 64, kAlign);
-    size_t off_norm = align_up(off_wl + sizeof(float) * kMaxSources * (size_t)cap, kAlign);
+    size_t off_norm = align_up(off_wl + sizeof(double) * kMaxSources * (size_t)cap, kAlign);
     size_t off_g = align_up(off_norm + sizeof(double) * (size_t)cap, kAlign);
-    size_t off_src = align_up(off_g + sizeof(float) * (size_t)(D.nx + D.ny + D.nz), kAlign);
+    size_t off_src = align_up(off_g + sizeof(double) * (size_t)(D.nx + D.ny + D.nz), kAlign);
     size_t off_halo = align_up(off_src + sizeof(int4) * kMaxSources, kAlign);
     size_t total = align_up(off_halo + sizeof(HaloDesc) * 6 * (size_t)nsub, kAlign);
     char *m = nullptr;
@@ -635,21 +636,22 @@ gw_status gw_domain_create(gw_ctx *c, const gw_shot_desc *desc, int px, int py,
     d->d_err = reinterpret_cast<unsigned *>(m + off_err);
     d->d_step = reinterpret_cast<int *>(m + off_step);
     d->d_scratch = reinterpret_cast<double *>(m + off_scr);
-    d->d_wavelet = reinterpret_cast<float *>(m + off_wl);
+    d->d_wavelet = reinterpret_cast<double *>(m + off_wl);
     d->d_norms = reinterpret_cast<double *>(m + off_norm);
-    d->d_gtab = reinterpret_cast<float *>(m + off_g);
+    d->d_gtab = reinterpret_cast<double *>(m + off_g);
     d->d_src = reinterpret_cast<int4 *>(m + off_src);
     d->d_halo = reinterpret_cast<HaloDesc *>(m + off_halo);
 
-    // sponge tables on global coordinates, FP64 -> FP32
+    // sponge tables on global coordinates, FP64 (the kernels round them to
+    // their arithmetic type when they load them)
     {
-        std::vector<float> g(D.nx + D.ny + D.nz);
+        std::vector<double> g(D.nx + D.ny + D.nz);
         const int n3[3] = {D.nx, D.ny, D.nz};
         size_t o = 0;
         for (int a = 0; a < 3; ++a)
             for (int i = 0; i < n3[a]; ++i)
-                g[o++] = (float)cerjan(i, n3[a], D.sponge, d->desc.sponge_a);
-        e = cudaMemcpy(d->d_gtab, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice);
+                g[o++] = cerjan(i, n3[a], D.sponge, d->desc.sponge_a);
+        e = cudaMemcpy(d->d_gtab, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail_out(cuda_fail(e, "cudaMemcpy"));
     }
     ShotDev &sh = d->shot;
@@ -799,13 +801,10 @@ static void choose_scales(gw_domain *d)
     } else {
         double amp = 0.0;
         const double cmax = d->courant * d->courant;
-        for (size_t s = 0; s < d->srcs.size(); ++s) {
-            double acc = 0.0;
+        for (const std::vector<double> &w : d->wavelets) {
             // sum of |wavelet| bounds the accumulated kick at the source
-            std::vector<float> w(d->shot.cap);
-            cudaMemcpy(w.data(), d->d_wavelet + s * d->shot.cap,
-                       sizeof(float) * d->shot.cap, cudaMemcpyDeviceToHost);
-            for (float v : w) acc += std::fabs((double)v);
+            double acc = 0.0;
+            for (double v : w) acc += std::fabs(v);
             amp += cmax * acc;
         }
         if (amp <= 0) amp = 1.0;
@@ -822,30 +821,53 @@ static void choose_scales(gw_domain *d)
     d->shot.isw = (float)(1.0 / d->sw);
 }
 
-gw_status gw_inject_source(gw_domain *d, int gx, int gy, int gz,
-                           const float *wavelet, int n)
+static gw_status add_source(gw_domain *d, int gx, int gy, int gz,
+                            std::vector<double> w)
 {
     GW_TRY(check_dom(d));
     const gw_shot_desc &D = d->desc;
     if (gx < 0 || gy < 0 || gz < 0 || gx >= D.nx || gy >= D.ny || gz >= D.nz)
         return fail(GW_ERR_ARG, "source (%d, %d, %d) outside the grid", gx, gy, gz);
     if ((int)d->srcs.size() >= kMaxSources) return fail(GW_ERR_ARG, "too many sources");
-    if (n < 0 || (n && !wavelet)) return fail(GW_ERR_ARG, "bad wavelet");
     if (d->step != 0 && d->dtype == DT_F16S)
         return fail(GW_ERR_STATE, "FP16 scales are fixed once stepping started");
     std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
     GW_TRY(sync_dom(d));
     int idx = (int)d->srcs.size();
-    std::vector<float> w(d->shot.cap, 0.0f);
-    for (int i = 0; i < std::min(n, d->shot.cap); ++i) w[i] = wavelet[i];
+    w.resize(d->shot.cap, 0.0);
     GW_TRY_CUDA(cudaMemcpy(d->d_wavelet + (size_t)idx * d->shot.cap, w.data(),
-                           sizeof(float) * w.size(), cudaMemcpyHostToDevice));
+                           sizeof(double) * w.size(), cudaMemcpyHostToDevice));
     d->srcs.push_back(make_int4(gx, gy, gz, 0));
+    d->wavelets.push_back(std::move(w));
     GW_TRY_CUDA(cudaMemcpy(d->d_src, d->srcs.data(), sizeof(int4) * d->srcs.size(),
                            cudaMemcpyHostToDevice));
     d->shot.nsrc = (int)d->srcs.size();
     choose_scales(d);
     return push_shot(d);
+}
+
+gw_status gw_inject_source(gw_domain *d, int gx, int gy, int gz,
+                           const float *wavelet, int n)
+{
+    if (!d) return fail(GW_ERR_ARG, "domain is NULL");
+    if (n < 0 || (n && !wavelet)) return fail(GW_ERR_ARG, "bad wavelet");
+    std::vector<double> w(wavelet, wavelet + n);
+    return add_source(d, gx, gy, gz, std::move(w));
+}
+
+gw_status gw_inject_ricker(gw_domain *d, int gx, int gy, int gz, double f_peak)
+{
+    if (!d) return fail(GW_ERR_ARG, "domain is NULL");
+    if (!d->model_set) return fail(GW_ERR_STATE, "set the velocity model first (dt)");
+    if (!(f_peak > 0)) return fail(GW_ERR_ARG, "peak frequency must be positive");
+    std::vector<double> w(d->shot.cap);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < d->shot.cap; ++i) {
+        double tau = i * d->dt - 1.0 / f_peak;
+        double a = pi * pi * f_peak * f_peak * tau * tau;
+        w[i] = (1.0 - 2.0 * a) * std::exp(-a);
+    }
+    return add_source(d, gx, gy, gz, std::move(w));
 }
 
 gw_status gw_set_receivers(gw_domain *d, int nrec, const int *xyz)

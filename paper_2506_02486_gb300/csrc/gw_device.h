@@ -54,10 +54,11 @@ struct SubDev {
 
 struct ShotDev {
     int *step;             // device step counter n (steps taken)
-    const float *wavelet;  // [nsrc][cap]
+    const double *wavelet; // [nsrc][cap] source samples
     float *traces;         // [nrec][cap]
     double *norms;         // [cap] per-step sum of u_{n+1}^2
-    const float *gx, *gy, *gz;   // global sponge profiles (FP32)
+    const double *gx, *gy, *gz;  // global sponge profiles (rounded to the
+                                 // math type when loaded)
     const int4 *src;       // nsrc (x, y, z, 0) global cells
     const int4 *rec;       // nrec (x, y, z, 0) global cells
     int cap;               // capacity of wavelet / traces / norms

@@ -201,11 +201,20 @@ struct Step {
     bool aborted;              // this thread's wait gave up
     bool cta_abort;            // some thread's wait gave up (CTA-uniform)
 
-    // current item
+    // current item (cached in registers: the stores below may alias the
+    // global tables, so nothing is re-read from them inside the z loop)
     int sub, x0, y0, z0, z1, n, par;
     int nx, ny, nz;
     int vx;                    // valid x points of this thread (0..4)
     bool rowok[PY];
+    int px_;                   // row pitch (elements)
+    size_t plane_;             // plane stride (elements)
+    int nbr_[6];
+    int rank_;
+    M isu_, isw_, su_, sw_;
+    const double *gz_ptr;      // sponge factors along z of this subdomain
+    M gz_next;                 // sponge factor of the next plane (prefetched)
+    int cap_;
     const SubDev *sd;
     const ShotDev *sh;
     T *unext, *wbuf;
@@ -323,6 +332,16 @@ struct Step {
         z0 = I.z0;
         z1 = I.z1;
         nx = sd->nx; ny = sd->ny; nz = sd->nz;
+        px_ = sd->px;
+        plane_ = (size_t)sd->px * sd->py;
+        rank_ = sd->rank;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) nbr_[f] = sd->nbr[f];
+        isu_ = (M)sh->isu; isw_ = (M)sh->isw;
+        su_ = (M)sh->su;   sw_ = (M)sh->sw;
+        cap_ = sh->cap;
+        gz_ptr = sh->gz + sd->gz0;
+        if (SPONGE) gz_next = (M)__ldg(gz_ptr + z0);
         n = *sh->step + A.k;
         par = n & 1;
         unext = reinterpret_cast<T *>(sd->u[par ^ 1]);
@@ -428,7 +447,10 @@ struct Step {
                         (PY * ty + r) * TX + 4 * tx, cf[r]);
             }
             M gz = M(1);
-            if (SPONGE) gz = (M)__ldg(sh->gz + sd->gz0 + z);
+            if (SPONGE) {
+                gz = gz_next;                       // loaded one plane ago
+                if (z + 1 < z1) gz_next = (M)__ldg(gz_ptr + z + 1);
+            }
 
             M lap[PY][4];
 #pragma unroll
@@ -453,7 +475,7 @@ struct Step {
                     l = fma_rn(W<M>::c3, s[3], l);
                     l = fma_rn(W<M>::c4, s[4], l);
                     // delta storage holds su * u: undo the power-of-two scale
-                    if (DELTA) l = mul_rn(l, (M)sh->isu);
+                    if (DELTA) l = mul_rn(l, isu_);
                     lap[r][i] = l;
                 }
             }
@@ -463,8 +485,8 @@ struct Step {
                 int4 q = loc()[e];
                 if (q.x < 0 && q.z == z) {
                     int lx = q.y & 0xffff, ly = q.y >> 16;
-                    if ((lx >> 2) == tx && ly / PY == ty && n < sh->cap) {
-                        M wv = (M)__ldg(sh->wavelet + (size_t)(-1 - q.x) * sh->cap + n);
+                    if ((lx >> 2) == tx && ly / PY == ty && n < cap_) {
+                        M wv = (M)__ldg(sh->wavelet + (size_t)(-1 - q.x) * cap_ + n);
 #pragma unroll
                         for (int r = 0; r < PY; ++r)
 #pragma unroll
@@ -483,8 +505,8 @@ struct Step {
                     M G = SPONGE ? mul_rn(gxy[r][i], gz) : M(1);
                     M u = yv[r + R][i];
                     if (DELTA) {
-                        M w = mul_rn(pa[r][i], (M)sh->isw);
-                        M uu = mul_rn(u, (M)sh->isu);
+                        M w = mul_rn(pa[r][i], isw_);
+                        M uu = mul_rn(u, isu_);
                         M a = fma_rn(cf[r][i], lap[r][i], w);
                         wn[r][i] = SPONGE ? mul_rn(G, a) : a;
                         un[r][i] = SPONGE ? fma_rn(G, uu, wn[r][i])
@@ -498,28 +520,30 @@ struct Step {
                 }
             }
             // stores: u' (and w') at this plane; norm partial
-            const size_t plane = (size_t)sd->px * sd->py;
 #pragma unroll
             for (int r = 0; r < PY; ++r) {
                 if (!rowok[r] || vx == 0) continue;
                 const int y = y0 + PY * ty + r;
                 const int x = x0 + 4 * tx;
-                const size_t off = (size_t)(z + R) * plane +
-                                   (size_t)(y + R) * sd->px + XO + x;
+                const size_t off = (size_t)(z + R) * plane_ +
+                                   (size_t)(y + R) * px_ + XO + x;
                 M so[4], sw[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    so[i] = DELTA ? mul_rn(un[r][i], (M)sh->su) : un[r][i];
-                    sw[i] = DELTA ? mul_rn(wn[r][i], (M)sh->sw) : M(0);
+                    so[i] = DELTA ? mul_rn(un[r][i], su_) : un[r][i];
+                    sw[i] = DELTA ? mul_rn(wn[r][i], sw_) : M(0);
                     if (i < vx) acc = fma_rn(un[r][i], un[r][i], acc);
                 }
                 if (vx == 4) {
                     S::st4(unext + off, so);
                     if (DELTA) S::st4(wbuf + off, sw);
                 } else {
-                    for (int i = 0; i < vx; ++i) {
-                        S::st1(unext + off + i, so[i]);
-                        if (DELTA) S::st1(wbuf + off + i, sw[i]);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (i < vx) {
+                            S::st1(unext + off + i, so[i]);
+                            if (DELTA) S::st1(wbuf + off + i, sw[i]);
+                        }
                     }
                 }
                 if (A.fused_halo) put_halo_row(x, y, z, so);
@@ -529,14 +553,14 @@ struct Step {
                 int4 q = loc()[e];
                 if (q.x >= 0 && q.z == z) {
                     int lx = q.y & 0xffff, ly = q.y >> 16;
-                    if ((lx >> 2) == tx && ly / PY == ty && n < sh->cap) {
+                    if ((lx >> 2) == tx && ly / PY == ty && n < cap_) {
                         M v = M(0);
 #pragma unroll
                         for (int r = 0; r < PY; ++r)
 #pragma unroll
                             for (int i = 0; i < 4; ++i)
                                 if (r == ly % PY && i == (lx & 3)) v = un[r][i];
-                        sh->traces[(size_t)q.x * sh->cap + n] = (float)v;
+                        sh->traces[(size_t)q.x * cap_ + n] = (float)v;
                     }
                 }
             }
@@ -553,45 +577,52 @@ struct Step {
 
     // One-sided puts of a freshly computed row segment into the halos of
     // the face neighbours that read it (Listing 1's ompx_put, fused).
-    __device__ void put_row(int nb, int x, int y, int z, const M so[4],
-                            int ncount, bool vec)
+    // mask selects which of the 4 points to store; all4 stores one vector.
+    __device__ void put_row(int nb, int x, int y, int z, const M (&so)[4],
+                            unsigned mask, bool all4)
     {
         const SubDev &o = A.subs[nb];
         T *base;
         if (A.symmetric)
             base = reinterpret_cast<T *>(
                 reinterpret_cast<char *>(unext) +
-                (long long)(o.rank - sd->rank) * A.rank_stride);
+                (long long)(o.rank - rank_) * A.rank_stride);
         else
             base = reinterpret_cast<T *>(o.u[par ^ 1]);
         const size_t off = ((size_t)(z + R) * o.py + (size_t)(y + R)) * o.px + XO + x;
-        if (vec) {
+        if (all4) {
             S::st4(base + off, so);
         } else {
-            for (int i = 0; i < ncount; ++i) S::st1(base + off + i, so[i]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (mask >> i & 1u) S::st1(base + off + i, so[i]);
         }
     }
 
-    __device__ void put_halo_row(int x, int y, int z, const M so[4])
+    __device__ void put_halo_row(int x, int y, int z, const M (&so)[4])
     {
-        const int *nb = sd->nbr;
-        const bool vec = vx == 4;
-        if (z < R && nb[4] >= 0)
-            put_row(nb[4], x, y, A.subs[nb[4]].nz + z, so, vx, vec);
-        if (z >= nz - R && nb[5] >= 0)
-            put_row(nb[5], x, y, z - nz, so, vx, vec);
-        if (y < R && nb[2] >= 0)
-            put_row(nb[2], x, A.subs[nb[2]].ny + y, z, so, vx, vec);
-        if (y >= ny - R && nb[3] >= 0)
-            put_row(nb[3], x, y - ny, z, so, vx, vec);
-        if (x < R && nb[0] >= 0) {
-            const int onx = A.subs[nb[0]].nx;
-            for (int i = 0; i < vx; ++i)
-                if (x + i < R) put_row(nb[0], onx + x + i, y, z, so + i, 1, false);
+        const bool all4 = vx == 4;
+        const unsigned valid = (1u << vx) - 1u;
+        if (z < R && nbr_[4] >= 0)
+            put_row(nbr_[4], x, y, A.subs[nbr_[4]].nz + z, so, valid, all4);
+        if (z >= nz - R && nbr_[5] >= 0)
+            put_row(nbr_[5], x, y, z - nz, so, valid, all4);
+        if (y < R && nbr_[2] >= 0)
+            put_row(nbr_[2], x, A.subs[nbr_[2]].ny + y, z, so, valid, all4);
+        if (y >= ny - R && nbr_[3] >= 0)
+            put_row(nbr_[3], x, y - ny, z, so, valid, all4);
+        if (x < R && nbr_[0] >= 0) {
+            // points x + i < R go to the -x neighbour's +x halo
+            unsigned m = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) m |= (x + i < R ? 1u : 0u) << i;
+            put_row(nbr_[0], A.subs[nbr_[0]].nx + x, y, z, so, m & valid, false);
         }
-        if (x + vx > nx - R && nb[1] >= 0) {
-            for (int i = 0; i < vx; ++i)
-                if (x + i >= nx - R) put_row(nb[1], x + i - nx, y, z, so + i, 1, false);
+        if (x + vx > nx - R && nbr_[1] >= 0) {
+            unsigned m = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) m |= (x + i >= nx - R ? 1u : 0u) << i;
+            put_row(nbr_[1], x - nx, y, z, so, m & valid, false);
         }
     }
 

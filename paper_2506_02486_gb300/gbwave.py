@@ -103,6 +103,7 @@ _SIGS = {
     "gw_set_model_f32": [_P, _P],
     "gw_ricker": [_D, _D, _I, _P],
     "gw_inject_source": [_P, _I, _I, _I, _P, _I],
+    "gw_inject_ricker": [_P, _I, _I, _I, _D],
     "gw_set_receivers": [_P, _I, _P],
     "gw_step": [_P, _I, _P],
     "gw_put_halo": [_P, _P],
@@ -334,6 +335,11 @@ def gw_inject_source(dom: int, gx: int, gy: int, gz: int, wavelet):
     w = np.ascontiguousarray(wavelet, dtype=np.float32)
     _check(lib().gw_inject_source(dom, int(gx), int(gy), int(gz), _ptr(w),
                                   int(w.size)), "gw_inject_source")
+
+
+def gw_inject_ricker(dom: int, gx: int, gy: int, gz: int, f_peak: float):
+    _check(lib().gw_inject_ricker(dom, int(gx), int(gy), int(gz),
+                                  float(f_peak)), "gw_inject_ricker")
 
 
 def gw_set_receivers(dom: int, xyz):

@@ -83,11 +83,9 @@ class Shot:
     def set_model(self, vel: np.ndarray):
         gw.gw_set_model(self.dom, vel)
 
-    def add_ricker(self, pos, f_peak: float, nsteps: int | None = None):
-        n = self.desc.nsteps if nsteps is None else nsteps
-        w = gw.gw_ricker(f_peak, self.info["dt"], n)
-        gw.gw_inject_source(self.dom, *pos, w)
-        return w
+    def add_ricker(self, pos, f_peak: float):
+        """The library's FP64 Ricker source (sampled at the domain's dt)."""
+        gw.gw_inject_ricker(self.dom, *pos, f_peak)
 
     def add_source(self, pos, wavelet):
         gw.gw_inject_source(self.dom, *pos, wavelet)

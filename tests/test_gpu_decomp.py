@@ -44,7 +44,9 @@ def test_decomposed_equals_undecomposed(reference, px, py, pz, symmetric,
     assert g["info"]["nsub"] == px * py * pz
     assert np.array_equal(g["u32"], base["u32"])
     assert np.array_equal(g["traces"], base["traces"])
-    assert g["norms"] == pytest.approx(base["norms"], rel=1e-12)
+    # norms are FP64 sums of per-thread FP32 partials, grouped by tile:
+    # equal to rounding only
+    assert g["norms"] == pytest.approx(base["norms"], rel=1e-6)
 
 
 @pytest.mark.parametrize("symmetric", [True, False])
