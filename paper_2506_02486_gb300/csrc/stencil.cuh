@@ -21,8 +21,8 @@
 // Thread 0 issues loads SU - 5 planes ahead of the consumers, across item
 // boundaries.  Each thread owns 4 consecutive x points (one 128-bit group
 // for FP32) of PY rows.  Its z neighbours come from a 9-deep register queue
-// filled from the plane that just arrived (the rotation is compile-time,
-// by unrolling over 9 phases); x/y neighbours come from the staged plane.
+// filled from the plane that just arrived; x/y neighbours come from the
+// staged plane.
 //
 // Arithmetic order (fixed, so that decomposed and undecomposed runs and
 // mirror-image points give identical bits):
@@ -411,11 +411,12 @@ struct Step {
     }
 
     // ---- one u-plane iteration -----------------------------------------
-    // Phase PH = t mod 9 fixes where plane t lands in the register queue.
-    template <int PH>
+    // The register queue Q[0..8] holds this thread's points on planes
+    // z-4 .. z+4; the plane that just arrived lands in Q[8] and the queue
+    // shifts down one plane per iteration (a compact loop body keeps the
+    // hot loop inside the instruction cache).
     __device__ __forceinline__ void iter(int t)
     {
-        if (cta_abort) return;   // a wait gave up: leave uniformly
         // (1) the plane of load t: append its centre values to the queue
         {
             unsigned slot = tg % SU;
@@ -423,7 +424,7 @@ struct Step {
             const T *pl = ubuf(slot);
 #pragma unroll
             for (int r = 0; r < PY; ++r)
-                S::ld4(pl + (PY * ty + r + R) * C::RW + XO + 4 * tx, Q[PH][r]);
+                S::ld4(pl + (PY * ty + r + R) * C::RW + XO + 4 * tx, Q[8][r]);
         }
         // (2) compute plane z = z0 + t - 8 once the queue is full
         if (t >= 2 * R) {
@@ -464,8 +465,8 @@ struct Step {
                         M xp = (i + m <= 3) ? yv[r + R][i + m] : rt[r][i + m - 4];
                         M ym = yv[r + R - m][i];
                         M yp = yv[r + R + m][i];
-                        M zm = Q[(PH + 9 - R - m) % 9][r][i];
-                        M zp = Q[(PH + 9 - R + m) % 9][r][i];
+                        M zm = Q[R - m][r][i];
+                        M zp = Q[R + m][r][i];
                         s[m] = add_rn(add_rn(add_rn(xm, xp), add_rn(ym, yp)),
                                       add_rn(zm, zp));
                     }
@@ -566,6 +567,13 @@ struct Step {
             }
             ++jg;
         }
+        // (3) shift the queue by one plane
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int r = 0; r < PY; ++r)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) Q[q][r][i] = Q[q + 1][r][i];
         ++tg;
         // the barrier also votes: every thread learns whether any wait gave up
         cta_abort = __syncthreads_or(aborted) != 0;
@@ -578,7 +586,7 @@ struct Step {
     // One-sided puts of a freshly computed row segment into the halos of
     // the face neighbours that read it (Listing 1's ompx_put, fused).
     // mask selects which of the 4 points to store; all4 stores one vector.
-    __device__ void put_row(int nb, int x, int y, int z, const M (&so)[4],
+    __device__ __forceinline__ void put_row(int nb, int x, int y, int z, const M (&so)[4],
                             unsigned mask, bool all4)
     {
         const SubDev &o = A.subs[nb];
@@ -599,7 +607,7 @@ struct Step {
         }
     }
 
-    __device__ void put_halo_row(int x, int y, int z, const M (&so)[4])
+    __device__ __forceinline__ void put_halo_row(int x, int y, int z, const M (&so)[4])
     {
         const bool all4 = vx == 4;
         const unsigned valid = (1u << vx) - 1u;
@@ -653,17 +661,10 @@ struct Step {
         for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
             begin_item(it);
             const int T = z1 - z0 + 2 * R;
-            for (int tb = 0; tb < T; tb += 9) {
-                iter<0>(tb);
-                if (tb + 1 < T) iter<1>(tb + 1);
-                if (tb + 2 < T) iter<2>(tb + 2);
-                if (tb + 3 < T) iter<3>(tb + 3);
-                if (tb + 4 < T) iter<4>(tb + 4);
-                if (tb + 5 < T) iter<5>(tb + 5);
-                if (tb + 6 < T) iter<6>(tb + 6);
-                if (tb + 7 < T) iter<7>(tb + 7);
-                if (tb + 8 < T) iter<8>(tb + 8);
-                if (cta_abort) break;
+#pragma unroll 1
+            for (int t = 0; t < T; ++t) {
+                iter(t);
+                if (cta_abort) break;   // a wait gave up: leave uniformly
             }
             if (cta_abort) break;
             end_item(it);
