@@ -211,6 +211,8 @@ struct Step {
     size_t plane_;             // plane stride (elements)
     int nbr_[6];
     int rank_;
+    bool item_puts;            // fused puts: this tile touches a face with a neighbour
+    size_t roff_[PY];          // in-plane element offset of each row's first point
     M isu_, isw_, su_, sw_;
     const double *gz_ptr;      // sponge factors along z of this subdomain
     M gz_next;                 // sponge factor of the next plane (prefetched)
@@ -220,6 +222,7 @@ struct Step {
     T *unext, *wbuf;
     M gxy[PY][4];
     M acc;
+    float2 acc2;               // packed FP32 norm partials
     M Q[9][PY][4];
 
     __device__ Step(const StepArgs &a, unsigned char *sm) : A(a), smem(sm) {}
@@ -349,7 +352,14 @@ struct Step {
         int xs = x0 + 4 * tx;
         vx = min(4, max(0, nx - xs));
 #pragma unroll
-        for (int r = 0; r < PY; ++r) rowok[r] = (y0 + PY * ty + r) < ny;
+        for (int r = 0; r < PY; ++r) {
+            rowok[r] = (y0 + PY * ty + r) < ny;
+            roff_[r] = (size_t)(y0 + PY * ty + r + R) * px_ + XO + xs;
+        }
+        item_puts = A.fused_halo &&
+                    ((x0 < R && nbr_[0] >= 0) || (x0 + TX > nx - R && nbr_[1] >= 0) ||
+                     (y0 < R && nbr_[2] >= 0) || (y0 + TY > ny - R && nbr_[3] >= 0) ||
+                     (z0 < R && nbr_[4] >= 0) || (z1 > nz - R && nbr_[5] >= 0));
         if (SPONGE) {
 #pragma unroll
             for (int r = 0; r < PY; ++r) {
@@ -363,6 +373,7 @@ struct Step {
             }
         }
         acc = M(0);
+        acc2 = make_float2(0.0f, 0.0f);
         // receivers and sources inside this item -> shared list (warp 0)
         if (tid < 32) {
             int cnt = 0;
@@ -398,7 +409,7 @@ struct Step {
 
     __device__ void end_item(int it)
     {
-        double v = (double)acc;
+        double v = (double)acc + (double)acc2.x + (double)acc2.y;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if ((tid & 31) == 0) red()[tid >> 5] = v;
@@ -408,6 +419,138 @@ struct Step {
             for (int w = 0; w < C::NT / 32; ++w) s += red()[w];
             A.partials[(size_t)A.k * A.nitems + it] = s;
         }
+    }
+
+    // ---- arithmetic of one row of 4 points ---------------------------
+    // FP32 math runs on packed pairs (Blackwell f32x2 add/mul/fma, each lane
+    // rounded once to nearest: the same bits as the scalar order below).
+    // The x pair sums stay scalar so that no operand needs re-pairing.
+    __device__ __forceinline__ void laplacian_row(const M (&yv)[PY + 8][4],
+                                                  const M (&lf)[4],
+                                                  const M (&rt)[4], int r,
+                                                  M (&out)[4])
+    {
+        M sx[5][4];
+#pragma unroll
+        for (int m = 1; m <= 4; ++m)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                M xm = (i - m >= 0) ? yv[r + R][i - m] : lf[4 + i - m];
+                M xp = (i + m <= 3) ? yv[r + R][i + m] : rt[i + m - 4];
+                sx[m][i] = add_rn(xm, xp);
+            }
+        if constexpr (std::is_same<M, float>::value) {
+            const float2 c0 = make_float2(W<M>::c0x3, W<M>::c0x3);
+            const float2 c1 = make_float2(W<M>::c1, W<M>::c1);
+            const float2 c2 = make_float2(W<M>::c2, W<M>::c2);
+            const float2 c3 = make_float2(W<M>::c3, W<M>::c3);
+            const float2 c4 = make_float2(W<M>::c4, W<M>::c4);
+#pragma unroll
+            for (int h = 0; h < 4; h += 2) {
+                float2 S[5];
+#pragma unroll
+                for (int m = 1; m <= 4; ++m) {
+                    float2 sy = __fadd2_rn(make_float2(yv[r + R - m][h], yv[r + R - m][h + 1]),
+                                           make_float2(yv[r + R + m][h], yv[r + R + m][h + 1]));
+                    float2 sz = __fadd2_rn(make_float2(Q[R - m][r][h], Q[R - m][r][h + 1]),
+                                           make_float2(Q[R + m][r][h], Q[R + m][r][h + 1]));
+                    S[m] = __fadd2_rn(__fadd2_rn(make_float2(sx[m][h], sx[m][h + 1]), sy), sz);
+                }
+                float2 c = make_float2(yv[r + R][h], yv[r + R][h + 1]);
+                float2 l = __ffma2_rn(c1, S[1], __fmul2_rn(c0, c));
+                l = __ffma2_rn(c2, S[2], l);
+                l = __ffma2_rn(c3, S[3], l);
+                l = __ffma2_rn(c4, S[4], l);
+                // delta storage holds su * u: undo the power-of-two scale
+                if (DELTA) l = __fmul2_rn(l, make_float2(isu_, isu_));
+                out[h] = l.x;
+                out[h + 1] = l.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                M s[5];
+#pragma unroll
+                for (int m = 1; m <= 4; ++m)
+                    s[m] = add_rn(add_rn(sx[m][i], add_rn(yv[r + R - m][i], yv[r + R + m][i])),
+                                  add_rn(Q[R - m][r][i], Q[R + m][r][i]));
+                M l = fma_rn(W<M>::c1, s[1], mul_rn(W<M>::c0x3, yv[r + R][i]));
+                l = fma_rn(W<M>::c2, s[2], l);
+                l = fma_rn(W<M>::c3, s[3], l);
+                l = fma_rn(W<M>::c4, s[4], l);
+                if (DELTA) l = mul_rn(l, isu_);
+                out[i] = l;
+            }
+        }
+    }
+
+    // 3-level: u' = G (2u - G u_prev + coef lap);
+    // delta:   w' = G (w + coef lap),  u' = G u + w'.
+    __device__ __forceinline__ void update_row(const M (&u)[4], const M (&pa)[4],
+                                               const M (&cf)[4], const M (&lap)[4],
+                                               const M (&gxy)[4], M gz, M (&un)[4],
+                                               M (&wn)[4])
+    {
+        if constexpr (std::is_same<M, float>::value) {
+#pragma unroll
+            for (int h = 0; h < 4; h += 2) {
+                const float2 U = make_float2(u[h], u[h + 1]);
+                const float2 P = make_float2(pa[h], pa[h + 1]);
+                const float2 CF = make_float2(cf[h], cf[h + 1]);
+                const float2 L = make_float2(lap[h], lap[h + 1]);
+                float2 G = make_float2(1.0f, 1.0f);
+                if (SPONGE) G = __fmul2_rn(make_float2(gxy[h], gxy[h + 1]), make_float2(gz, gz));
+                float2 UN, WN = make_float2(0.0f, 0.0f);
+                if (DELTA) {
+                    const float2 w = __fmul2_rn(P, make_float2(isw_, isw_));
+                    const float2 uu = __fmul2_rn(U, make_float2(isu_, isu_));
+                    const float2 a = __ffma2_rn(CF, L, w);
+                    WN = SPONGE ? __fmul2_rn(G, a) : a;
+                    UN = SPONGE ? __ffma2_rn(G, uu, WN) : __fadd2_rn(uu, WN);
+                } else {
+                    // 2u - G u_prev rounded once: fma(-G, u_prev, u + u)
+                    const float2 nG = SPONGE ? make_float2(-G.x, -G.y)
+                                             : make_float2(-1.0f, -1.0f);
+                    const float2 tt = __ffma2_rn(nG, P, __fadd2_rn(U, U));
+                    const float2 a = __ffma2_rn(CF, L, tt);
+                    UN = SPONGE ? __fmul2_rn(G, a) : a;
+                }
+                un[h] = UN.x; un[h + 1] = UN.y;
+                wn[h] = WN.x; wn[h + 1] = WN.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                M G = SPONGE ? mul_rn(gxy[i], gz) : M(1);
+                if (DELTA) {
+                    M w = mul_rn(pa[i], isw_);
+                    M uu = mul_rn(u[i], isu_);
+                    M a = fma_rn(cf[i], lap[i], w);
+                    wn[i] = SPONGE ? mul_rn(G, a) : a;
+                    un[i] = SPONGE ? fma_rn(G, uu, wn[i]) : add_rn(uu, wn[i]);
+                } else {
+                    M tt = fma_rn(-G, pa[i], add_rn(u[i], u[i]));
+                    M a = fma_rn(cf[i], lap[i], tt);
+                    un[i] = SPONGE ? mul_rn(G, a) : a;
+                    wn[i] = M(0);
+                }
+            }
+        }
+    }
+
+    // sum of u'^2 over this thread's valid points (per-lane FP32 partials)
+    __device__ __forceinline__ void accumulate_norm(const M (&un)[4])
+    {
+        if constexpr (std::is_same<M, float>::value) {
+            if (vx == 4) {
+                acc2 = __ffma2_rn(make_float2(un[0], un[1]), make_float2(un[0], un[1]), acc2);
+                acc2 = __ffma2_rn(make_float2(un[2], un[3]), make_float2(un[2], un[3]), acc2);
+                return;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (i < vx) acc = fma_rn(un[i], un[i], acc);
     }
 
     // ---- one u-plane iteration -----------------------------------------
@@ -455,31 +598,7 @@ struct Step {
 
             M lap[PY][4];
 #pragma unroll
-            for (int r = 0; r < PY; ++r) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    M s[5];
-#pragma unroll
-                    for (int m = 1; m <= 4; ++m) {
-                        M xm = (i - m >= 0) ? yv[r + R][i - m] : lf[r][4 + i - m];
-                        M xp = (i + m <= 3) ? yv[r + R][i + m] : rt[r][i + m - 4];
-                        M ym = yv[r + R - m][i];
-                        M yp = yv[r + R + m][i];
-                        M zm = Q[R - m][r][i];
-                        M zp = Q[R + m][r][i];
-                        s[m] = add_rn(add_rn(add_rn(xm, xp), add_rn(ym, yp)),
-                                      add_rn(zm, zp));
-                    }
-                    M c = yv[r + R][i];
-                    M l = fma_rn(W<M>::c1, s[1], mul_rn(W<M>::c0x3, c));
-                    l = fma_rn(W<M>::c2, s[2], l);
-                    l = fma_rn(W<M>::c3, s[3], l);
-                    l = fma_rn(W<M>::c4, s[4], l);
-                    // delta storage holds su * u: undo the power-of-two scale
-                    if (DELTA) l = mul_rn(l, isu_);
-                    lap[r][i] = l;
-                }
-            }
+            for (int r = 0; r < PY; ++r) laplacian_row(yv, lf[r], rt[r], r, lap[r]);
             const int nl = misc()[0];
             // point sources: lap += wavelet[n] at the source cell
             for (int e = 0; e < nl; ++e) {
@@ -500,41 +619,21 @@ struct Step {
             // leapfrog update with the sponge
             M un[PY][4], wn[PY][4];
 #pragma unroll
-            for (int r = 0; r < PY; ++r) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    M G = SPONGE ? mul_rn(gxy[r][i], gz) : M(1);
-                    M u = yv[r + R][i];
-                    if (DELTA) {
-                        M w = mul_rn(pa[r][i], isw_);
-                        M uu = mul_rn(u, isu_);
-                        M a = fma_rn(cf[r][i], lap[r][i], w);
-                        wn[r][i] = SPONGE ? mul_rn(G, a) : a;
-                        un[r][i] = SPONGE ? fma_rn(G, uu, wn[r][i])
-                                          : add_rn(uu, wn[r][i]);
-                    } else {
-                        M tt = SPONGE ? fma_rn(-G, pa[r][i], add_rn(u, u))
-                                      : add_rn(add_rn(u, u), -pa[r][i]);
-                        M a = fma_rn(cf[r][i], lap[r][i], tt);
-                        un[r][i] = SPONGE ? mul_rn(G, a) : a;
-                    }
-                }
-            }
+            for (int r = 0; r < PY; ++r)
+                update_row(yv[r + R], pa[r], cf[r], lap[r], gxy[r], gz, un[r], wn[r]);
             // stores: u' (and w') at this plane; norm partial
+            const size_t zoff = (size_t)(z + R) * plane_;
 #pragma unroll
             for (int r = 0; r < PY; ++r) {
                 if (!rowok[r] || vx == 0) continue;
-                const int y = y0 + PY * ty + r;
-                const int x = x0 + 4 * tx;
-                const size_t off = (size_t)(z + R) * plane_ +
-                                   (size_t)(y + R) * px_ + XO + x;
+                const size_t off = zoff + roff_[r];
                 M so[4], sw[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     so[i] = DELTA ? mul_rn(un[r][i], su_) : un[r][i];
                     sw[i] = DELTA ? mul_rn(wn[r][i], sw_) : M(0);
-                    if (i < vx) acc = fma_rn(un[r][i], un[r][i], acc);
                 }
+                accumulate_norm(un[r]);
                 if (vx == 4) {
                     S::st4(unext + off, so);
                     if (DELTA) S::st4(wbuf + off, sw);
@@ -547,7 +646,7 @@ struct Step {
                         }
                     }
                 }
-                if (A.fused_halo) put_halo_row(x, y, z, so);
+                if (item_puts) put_halo_row(x0 + 4 * tx, y0 + PY * ty + r, z, so);
             }
             // receivers: trace[n] = u_{n+1}
             for (int e = 0; e < nl; ++e) {
