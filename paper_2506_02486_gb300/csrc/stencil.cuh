@@ -12,17 +12,19 @@
 // depth (their x/y halo strips are then served from L2), and CTA b takes
 // items b, b + grid, b + 2 grid, ...
 //
-// Per CTA, planes stream through two shared-memory rings filled by TMA
-// (cp.async.bulk.tensor, completion on mbarriers):
+// Warp specialisation.  Each CTA has NT/32 consumer warps and one producer
+// warp.  The producer streams, in consumption order and across item
+// boundaries, two rings of shared-memory slots filled by TMA
+// (cp.async.bulk.tensor, completion counted on "full" mbarriers):
 //   * the u ring (SU slots): plane p of u_n with its x/y halo, box
 //     (TX + 2 xoff) x (TY + 8);
 //   * the pointwise ring (SP slots): the TX x TY tiles of the second state
 //     field (u_{n-1}, or w_n for delta storage) and of coef at plane z.
-// Thread 0 issues loads SU - 5 planes ahead of the consumers, across item
-// boundaries.  Each thread owns 4 consecutive x points (one 128-bit group
-// for FP32) of PY rows.  Its z neighbours come from a 9-deep register queue
-// filled from the plane that just arrived; x/y neighbours come from the
-// staged plane.
+// Consumers hand slots back warp by warp through "empty" mbarriers, so no
+// CTA-wide barrier sits in the z loop.  Each consumer thread owns 4
+// consecutive x points (one 128-bit group for FP32) of PY rows.  Its z
+// neighbours come from a 9-deep register queue filled from the plane that
+// just arrived; x/y neighbours come from the staged plane.
 //
 // Arithmetic order (fixed, so that decomposed and undecomposed runs and
 // mirror-image points give identical bits):
@@ -31,7 +33,7 @@
 //   lap += wavelet[n] at a source cell
 //   3-level: u' = G * fma(coef, lap, fma(-G, u_prev, u + u))
 //   delta:   w' = G * fma(coef, lap, w);  u' = fma(G, u, w')
-// with G = (g_x g_y) g_z from per-axis FP32 tables on global coordinates.
+// with G = (g_x g_y) g_z from per-axis tables on global coordinates.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -157,6 +159,12 @@ struct Cfg {
     using CT = typename std::conditional<sizeof(T_) == 2, __half, T_>::type;
     static constexpr int TX = TX_, TY = TY_, PY = PY_, SU = SU_, SP = SP_;
     static constexpr int NTX = TX / 4, NTY = TY / PY, NT = NTX * NTY;
+    static constexpr int NCW = NT / 32;              // consumer warps
+    static constexpr int THREADS = NT + 32;          // + one producer warp
+    // registers per thread: the whole SM register file over THREADS
+    // threads, rounded down to the 8-register allocation unit
+    static constexpr int MAXREG_ = (65536 / THREADS) / 8 * 8;
+    static constexpr int MAXREG = MAXREG_ > 255 ? 255 : MAXREG_;
     static constexpr int XO = St<T>::XO;
     static constexpr int RW = TX + 2 * XO;          // smem row (elements)
     static constexpr int UROWS = TY + 2 * R;
@@ -164,15 +172,43 @@ struct Cfg {
     static constexpr int PBYTES = TX * TY * (int)sizeof(T);
     static constexpr int OFF_P = SU * UBYTES;
     static constexpr int OFF_BAR = OFF_P + SP * 2 * PBYTES;
-    static constexpr int OFF_LOC = OFF_BAR + 8 * (SU + SP);
+    static constexpr int OFF_LOC = OFF_BAR + 16 * (SU + SP);   // full + empty
     static constexpr int OFF_MISC = OFF_LOC + 16 * kMaxLocal;
     static constexpr int OFF_RED = OFF_MISC + 16;
-    static constexpr int SMEM = OFF_RED + 8 * (NT / 32);
+    static constexpr int SMEM = OFF_RED + 8 * NCW;
     static_assert(TX % 4 == 0 && TY % PY == 0 && NT % 32 == 0, "tile");
     static_assert(UBYTES % 128 == 0 && PBYTES % 128 == 0, "TMA alignment");
     static_assert((RW * (int)sizeof(T)) % 16 == 0, "TMA box row");
     static_assert(SU >= 6 && SP >= 2, "ring depth");
 };
+
+// Bounded wait that also gives up at once when another thread of the CTA
+// already gave up (shared abort flag): a timed-out CTA drains quickly.
+__device__ __forceinline__ bool wait_slot(uint64_t *bar, uint32_t parity,
+                                          volatile int *abortf)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    unsigned long long t0 = global_timer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63u) == 0) {
+            if (*abortf) return false;
+            if (global_timer() - t0 > kWaitLimitNs) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];"
+                 :: "r"(smem_addr(bar)) : "memory");
+}
+
+// Barrier among the consumer warps only (the producer warp is not part).
+__device__ __forceinline__ void consumer_sync(int nthreads)
+{
+    asm volatile("bar.sync 1, %0;" :: "r"(nthreads) : "memory");
+}
 
 // ---------------------------------------------------------------- kernel
 
@@ -186,20 +222,11 @@ struct Step {
 
     const StepArgs &A;
     unsigned char *smem;
-    int tid, tx, ty;
-
-    // producer (thread 0)
-    int lp_it, lp_t, lp_T, lp_x, lp_y, lp_z;
-    const char *lp_map;
-    int pp_it, pp_j, pp_J, pp_x, pp_y, pp_z;
-    const char *pp_map_a, *pp_map_b;
-    unsigned l_issued, p_issued;
-    uint64_t pol_first, pol_last;
+    int tid, tx, ty, lane;
 
     // consumer
     unsigned tg, jg;           // u loads / pointwise planes consumed
-    bool aborted;              // this thread's wait gave up
-    bool cta_abort;            // some thread's wait gave up (CTA-uniform)
+    bool aborted;              // a wait of this thread gave up
 
     // current item (cached in registers: the stores below may alias the
     // global tables, so nothing is re-read from them inside the z loop)
@@ -211,6 +238,7 @@ struct Step {
     size_t plane_;             // plane stride (elements)
     int nbr_[6];
     int rank_;
+    int nl_;                   // receivers + sources inside this item
     bool item_puts;            // fused puts: this tile touches a face with a neighbour
     size_t roff_[PY];          // in-plane element offset of each row's first point
     M isu_, isw_, su_, sw_;
@@ -236,91 +264,78 @@ struct Step {
         return reinterpret_cast<T *>(smem + C::OFF_P +
                                      (slot * 2 + f) * C::PBYTES);
     }
-    __device__ uint64_t *ufull(unsigned slot)
-    {
-        return reinterpret_cast<uint64_t *>(smem + C::OFF_BAR) + slot;
-    }
-    __device__ uint64_t *pfull(unsigned slot)
-    {
-        return reinterpret_cast<uint64_t *>(smem + C::OFF_BAR) + SU + slot;
-    }
+    __device__ uint64_t *bars() { return reinterpret_cast<uint64_t *>(smem + C::OFF_BAR); }
+    __device__ uint64_t *ufull(unsigned s) { return bars() + s; }
+    __device__ uint64_t *pfull(unsigned s) { return bars() + SU + s; }
+    __device__ uint64_t *uempty(unsigned s) { return bars() + SU + SP + s; }
+    __device__ uint64_t *pempty(unsigned s) { return bars() + 2 * SU + SP + s; }
     __device__ int4 *loc() { return reinterpret_cast<int4 *>(smem + C::OFF_LOC); }
     __device__ int *misc() { return reinterpret_cast<int *>(smem + C::OFF_MISC); }
+    __device__ volatile int *abortf() { return misc() + 1; }
     __device__ double *red() { return reinterpret_cast<double *>(smem + C::OFF_RED); }
 
-    __device__ int step_of(const Item &I) const
+    __device__ bool wait_or_abort(uint64_t *bar, uint32_t parity)
     {
-        const SubDev &s = A.subs[I.sub];
-        return *A.shots[s.shot].step + A.k;
-    }
-
-    // ---- producer -----------------------------------------------------
-    __device__ void lp_decode()
-    {
-        if (lp_it >= A.nitems) return;
-        Item I = A.items[lp_it];
-        int p = step_of(I) & 1;
-        lp_map = static_cast<const char *>(A.maps) +
-                 (size_t)(I.sub * kMapsPerSub + (p ? MAP_U1_HALO : MAP_U0_HALO)) * 128;
-        lp_x = I.xy & 0xffff;          // padded x of interior x0 - XO
-        lp_y = I.xy >> 16;             // padded y of interior y0 - R
-        lp_z = I.z0;                   // padded z of interior z0 - R
-        lp_T = I.z1 - I.z0 + 2 * R;
-        lp_t = 0;
-        tensormap_acquire(lp_map);
-    }
-    __device__ void pp_decode()
-    {
-        if (pp_it >= A.nitems) return;
-        Item I = A.items[pp_it];
-        int p = step_of(I) & 1;
-        const char *base = static_cast<const char *>(A.maps) +
-                           (size_t)I.sub * kMapsPerSub * 128;
-        int slot_a = DELTA ? MAP_W_PW : (p ? MAP_U0_PW : MAP_U1_PW);
-        pp_map_a = base + slot_a * 128;
-        pp_map_b = base + MAP_COEF_PW * 128;
-        pp_x = (I.xy & 0xffff) + XO;
-        pp_y = (I.xy >> 16) + R;
-        pp_z = I.z0 + R;
-        pp_J = I.z1 - I.z0;
-        pp_j = 0;
-        tensormap_acquire(pp_map_a);
-        tensormap_acquire(pp_map_b);
-    }
-    __device__ void issue_u()
-    {
-        if (lp_it >= A.nitems) return;
-        unsigned slot = l_issued % SU;
-        uint64_t *bar = ufull(slot);
-        mbar_arrive_expect_tx(bar, C::UBYTES);
-        tma_load_3d(ubuf(slot), lp_map, bar, lp_x, lp_y, lp_z + lp_t, pol_last);
-        ++l_issued;
-        if (++lp_t == lp_T) {
-            lp_it += gridDim.x;
-            lp_decode();
-        }
-    }
-    __device__ void issue_p()
-    {
-        if (pp_it >= A.nitems) return;
-        unsigned slot = p_issued % SP;
-        uint64_t *bar = pfull(slot);
-        mbar_arrive_expect_tx(bar, 2 * C::PBYTES);
-        tma_load_3d(pbuf(slot, 0), pp_map_a, bar, pp_x, pp_y, pp_z + pp_j, pol_first);
-        tma_load_3d(pbuf(slot, 1), pp_map_b, bar, pp_x, pp_y, pp_z + pp_j, pol_first);
-        ++p_issued;
-        if (++pp_j == pp_J) {
-            pp_it += gridDim.x;
-            pp_decode();
-        }
-    }
-
-    __device__ void wait_or_abort(uint64_t *bar, uint32_t parity)
-    {
-        if (!mbar_wait(bar, parity)) {
-            atomicOr(A.err, ERRB_TIMEOUT);
+        if (aborted) return false;
+        if (!wait_slot(bar, parity, abortf())) {
+            if (!*abortf()) atomicOr(A.err, ERRB_TIMEOUT);
+            *abortf() = 1;
             aborted = true;
+            return false;
         }
+        return true;
+    }
+
+    // ---- producer warp (one lane) ------------------------------------
+    __device__ void produce()
+    {
+        const uint64_t pol_first = policy_evict_first();
+        const uint64_t pol_last = policy_evict_last();
+        unsigned L = 0, P = 0;
+        for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
+            const Item I = A.items[it];
+            const SubDev &s = A.subs[I.sub];
+            const int p = (*A.shots[s.shot].step + A.k) & 1;
+            const char *base = static_cast<const char *>(A.maps) +
+                               (size_t)I.sub * kMapsPerSub * 128;
+            const char *map_u = base + (p ? MAP_U1_HALO : MAP_U0_HALO) * 128;
+            const char *map_a = base + (DELTA ? MAP_W_PW : (p ? MAP_U0_PW : MAP_U1_PW)) * 128;
+            const char *map_b = base + MAP_COEF_PW * 128;
+            tensormap_acquire(map_u);
+            tensormap_acquire(map_a);
+            tensormap_acquire(map_b);
+            const int ux = I.xy & 0xffff, uy = I.xy >> 16;   // padded box origin
+            const int T = I.z1 - I.z0 + 2 * R;
+            for (int t = 0; t < T; ++t) {
+                unsigned slot = L % SU;
+                if (L >= SU && !wait_slot(uempty(slot), ((L / SU) - 1) & 1u, abortf())) {
+                    *abortf() = 1;
+                    goto drain;
+                }
+                mbar_arrive_expect_tx(ufull(slot), C::UBYTES);
+                tma_load_3d(ubuf(slot), map_u, ufull(slot), ux, uy, I.z0 + t, pol_last);
+                ++L;
+                if (t >= 2 * R) {
+                    unsigned ps = P % SP;
+                    if (P >= SP && !wait_slot(pempty(ps), ((P / SP) - 1) & 1u, abortf())) {
+                        *abortf() = 1;
+                        goto drain;
+                    }
+                    mbar_arrive_expect_tx(pfull(ps), 2 * C::PBYTES);
+                    const int zz = I.z0 + t - R;   // padded z of interior z
+                    tma_load_3d(pbuf(ps, 0), map_a, pfull(ps), ux + XO, uy + R, zz, pol_first);
+                    tma_load_3d(pbuf(ps, 1), map_b, pfull(ps), ux + XO, uy + R, zz, pol_first);
+                    ++P;
+                }
+            }
+        }
+    drain:
+        // leave only after every copy issued into this CTA's shared memory
+        // has landed (bounded)
+        for (unsigned q = L > SU ? L - SU : 0; q < L; ++q)
+            if (!wait_slot(ufull(q % SU), (q / SU) & 1u, abortf())) break;
+        for (unsigned q = P > SP ? P - SP : 0; q < P; ++q)
+            if (!wait_slot(pfull(q % SP), (q / SP) & 1u, abortf())) break;
     }
 
     // ---- item set-up ----------------------------------------------------
@@ -377,7 +392,6 @@ struct Step {
         // receivers and sources inside this item -> shared list (warp 0)
         if (tid < 32) {
             int cnt = 0;
-            int lane = tid;
             int gxa = sd->gx0 + x0, gya = sd->gy0 + y0, gza = sd->gz0;
             int xl_end = min(TX, nx - x0), yl_end = min(TY, ny - y0);
             for (int pass = 0; pass < 2; ++pass) {
@@ -405,6 +419,8 @@ struct Step {
             }
             if (lane == 0) misc()[0] = min(cnt, kMaxLocal);
         }
+        consumer_sync(C::NT);
+        nl_ = misc()[0];
     }
 
     __device__ void end_item(int it)
@@ -412,11 +428,11 @@ struct Step {
         double v = (double)acc + (double)acc2.x + (double)acc2.y;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((tid & 31) == 0) red()[tid >> 5] = v;
-        __syncthreads();
+        if (lane == 0) red()[tid >> 5] = v;
+        consumer_sync(C::NT);
         if (tid == 0) {
             double s = 0.0;
-            for (int w = 0; w < C::NT / 32; ++w) s += red()[w];
+            for (int w = 0; w < C::NCW; ++w) s += red()[w];
             A.partials[(size_t)A.k * A.nitems + it] = s;
         }
     }
@@ -599,7 +615,7 @@ struct Step {
             M lap[PY][4];
 #pragma unroll
             for (int r = 0; r < PY; ++r) laplacian_row(yv, lf[r], rt[r], r, lap[r]);
-            const int nl = misc()[0];
+            const int nl = nl_;
             // point sources: lap += wavelet[n] at the source cell
             for (int e = 0; e < nl; ++e) {
                 int4 q = loc()[e];
@@ -664,7 +680,6 @@ struct Step {
                     }
                 }
             }
-            ++jg;
         }
         // (3) shift the queue by one plane
 #pragma unroll
@@ -673,13 +688,15 @@ struct Step {
             for (int r = 0; r < PY; ++r)
 #pragma unroll
                 for (int i = 0; i < 4; ++i) Q[q][r][i] = Q[q + 1][r][i];
-        ++tg;
-        // the barrier also votes: every thread learns whether any wait gave up
-        cta_abort = __syncthreads_or(aborted) != 0;
-        if (tid == 0 && !cta_abort) {
-            issue_u();
-            if (t >= 2 * R) issue_p();
+        // (4) hand slots back: load tg - 4 (its last use, as the x/y plane,
+        // was this iteration) and the pointwise tile just used
+        __syncwarp();
+        if (lane == 0) {
+            if (tg >= R) mbar_arrive(uempty((tg - R) % SU));
+            if (t >= 2 * R) mbar_arrive(pempty(jg % SP));
         }
+        if (t >= 2 * R) ++jg;
+        ++tg;
     }
 
     // One-sided puts of a freshly computed row segment into the halos of
@@ -736,50 +753,40 @@ struct Step {
     __device__ void run()
     {
         tid = threadIdx.x;
-        tx = tid % C::NTX;
-        ty = tid / C::NTX;
-        aborted = false;
-        cta_abort = false;
-        tg = jg = 0;
+        lane = tid & 31;
         if (tid == 0) {
-            for (int s = 0; s < SU; ++s) mbar_init(ufull(s), 1);
-            for (int s = 0; s < SP; ++s) mbar_init(pfull(s), 1);
+            for (int q = 0; q < SU; ++q) {
+                mbar_init(ufull(q), 1);
+                mbar_init(uempty(q), C::NCW);
+            }
+            for (int q = 0; q < SP; ++q) {
+                mbar_init(pfull(q), 1);
+                mbar_init(pempty(q), C::NCW);
+            }
+            misc()[1] = 0;
             fence_barrier_init();
         }
         __syncthreads();
-        if (tid == 0) {
-            pol_first = policy_evict_first();
-            pol_last = policy_evict_last();
-            l_issued = p_issued = 0;
-            lp_it = pp_it = blockIdx.x;
-            lp_decode();
-            pp_decode();
-            for (int i = 0; i < SU - 4; ++i) issue_u();
-            for (int i = 0; i < SP; ++i) issue_p();
+        if (tid >= C::NT) {            // the producer warp
+            if (tid == C::NT) produce();
+            return;
         }
+        tx = tid % C::NTX;
+        ty = tid / C::NTX;
+        aborted = false;
+        tg = jg = 0;
         for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
             begin_item(it);
             const int T = z1 - z0 + 2 * R;
 #pragma unroll 1
-            for (int t = 0; t < T; ++t) {
-                iter(t);
-                if (cta_abort) break;   // a wait gave up: leave uniformly
-            }
-            if (cta_abort) break;
+            for (int t = 0; t < T; ++t) iter(t);
             end_item(it);
-        }
-        // drain: wait (bounded) for every load still in flight
-        if (tid == 0) {
-            for (unsigned q = tg; q < l_issued; ++q)
-                if (!mbar_wait(ufull(q % SU), (q / SU) & 1u)) break;
-            for (unsigned q = jg; q < p_issued; ++q)
-                if (!mbar_wait(pfull(q % SP), (q / SP) & 1u)) break;
         }
     }
 };
 
 template <class C, bool DELTA, bool SPONGE>
-__global__ void __launch_bounds__(C::NT, 1)
+__global__ void __maxnreg__(C::MAXREG)
 k_step(const __grid_constant__ StepArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -790,7 +797,7 @@ k_step(const __grid_constant__ StepArgs a)
 template <class C>
 static TileInfo info_of()
 {
-    return TileInfo{C::TX, C::TY, C::NT, (size_t)C::SMEM};
+    return TileInfo{C::TX, C::TY, C::THREADS, (size_t)C::SMEM};
 }
 
 template <class C, bool DELTA>
@@ -805,7 +812,7 @@ static cudaError_t launch_cfg(bool sponge, int grid, const StepArgs &a,
         if (e != cudaSuccess) return e;
         attr_done[sponge] = true;
     }
-    kern<<<grid, C::NT, C::SMEM, s>>>(a);
+    kern<<<grid, C::THREADS, C::SMEM, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -817,7 +824,7 @@ static int occ_cfg(bool sponge)
                              C::SMEM) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, C::NT,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, C::THREADS,
                                                       C::SMEM) != cudaSuccess)
         return 0;
     return n;
