@@ -161,23 +161,26 @@ struct Cfg {
     static constexpr int NTX = TX / 4, NTY = TY / PY, NT = NTX * NTY;
     static constexpr int NCW = NT / 32;              // consumer warps
     static constexpr int THREADS = NT + 32;          // + one producer warp
-    // registers per thread: the whole SM register file over THREADS
-    // threads, rounded down to the 8-register allocation unit
-    static constexpr int MAXREG_ = (65536 / THREADS) / 8 * 8;
+    // registers per thread: each of the SM's 4 sub-partitions owns 16K
+    // registers and hosts ceil(warps / 4) of this CTA's warps
+    static constexpr int WPP = (THREADS / 32 + 3) / 4;
+    static constexpr int MAXREG_ = (16384 / (WPP * 32)) / 8 * 8;
     static constexpr int MAXREG = MAXREG_ > 255 ? 255 : MAXREG_;
     static constexpr int XO = St<T>::XO;
     static constexpr int RW = TX + 2 * XO;          // smem row (elements)
     static constexpr int UROWS = TY + 2 * R;
     static constexpr int UBYTES = RW * UROWS * (int)sizeof(T);
     static constexpr int PBYTES = TX * TY * (int)sizeof(T);
-    static constexpr int OFF_P = SU * UBYTES;
-    static constexpr int OFF_BAR = OFF_P + SP * 2 * PBYTES;
+    // slot strides padded to the 128-byte alignment of TMA destinations
+    static constexpr int USTRIDE = (UBYTES + 127) / 128 * 128;
+    static constexpr int PSTRIDE = (PBYTES + 127) / 128 * 128;
+    static constexpr int OFF_P = SU * USTRIDE;
+    static constexpr int OFF_BAR = OFF_P + SP * 2 * PSTRIDE;
     static constexpr int OFF_LOC = OFF_BAR + 16 * (SU + SP);   // full + empty
     static constexpr int OFF_MISC = OFF_LOC + 16 * kMaxLocal;
     static constexpr int OFF_RED = OFF_MISC + 16;
     static constexpr int SMEM = OFF_RED + 8 * NCW;
     static_assert(TX % 4 == 0 && TY % PY == 0 && NT % 32 == 0, "tile");
-    static_assert(UBYTES % 128 == 0 && PBYTES % 128 == 0, "TMA alignment");
     static_assert((RW * (int)sizeof(T)) % 16 == 0, "TMA box row");
     static_assert(SU >= 6 && SP >= 2, "ring depth");
 };
@@ -257,12 +260,12 @@ struct Step {
 
     __device__ T *ubuf(unsigned slot)
     {
-        return reinterpret_cast<T *>(smem + slot * C::UBYTES);
+        return reinterpret_cast<T *>(smem + slot * C::USTRIDE);
     }
     __device__ T *pbuf(unsigned slot, int f)
     {
         return reinterpret_cast<T *>(smem + C::OFF_P +
-                                     (slot * 2 + f) * C::PBYTES);
+                                     (slot * 2 + f) * C::PSTRIDE);
     }
     __device__ uint64_t *bars() { return reinterpret_cast<uint64_t *>(smem + C::OFF_BAR); }
     __device__ uint64_t *ufull(unsigned s) { return bars() + s; }

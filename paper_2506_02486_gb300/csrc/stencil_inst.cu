@@ -12,29 +12,29 @@ namespace gw {
 
 // Cfg<storage, tile x, tile y, rows per thread, u-ring slots, pointwise slots>
 #if GW_INST == 0
-using C = Cfg<float, 64, 32, 2, 8, 4>;  constexpr bool kDelta = false;
+using C = Cfg<float, 64, 28, 2, 8, 4>;  constexpr bool kDelta = false;
 #elif GW_INST == 1
-using C = Cfg<float, 64, 16, 2, 8, 4>;  constexpr bool kDelta = false;
+using C = Cfg<float, 128, 14, 2, 8, 4>; constexpr bool kDelta = false;
 #elif GW_INST == 2
-using C = Cfg<float, 128, 16, 2, 8, 4>; constexpr bool kDelta = false;
+using C = Cfg<float, 32, 56, 2, 8, 4>;  constexpr bool kDelta = false;
 #elif GW_INST == 3
-using C = Cfg<float, 32, 32, 2, 8, 4>;  constexpr bool kDelta = false;
+using C = Cfg<float, 64, 28, 2, 10, 5>; constexpr bool kDelta = false;
 #elif GW_INST == 4
 using C = Cfg<double, 32, 16, 1, 7, 3>; constexpr bool kDelta = false;
 #elif GW_INST == 5
 using C = Cfg<double, 64, 8, 1, 7, 3>;  constexpr bool kDelta = false;
 #elif GW_INST == 6
-using C = Cfg<__half, 64, 32, 2, 8, 4>;  constexpr bool kDelta = true;
+using C = Cfg<__half, 64, 28, 2, 8, 4>;  constexpr bool kDelta = true;
 #elif GW_INST == 7
-using C = Cfg<__half, 64, 16, 2, 8, 4>;  constexpr bool kDelta = true;
+using C = Cfg<__half, 128, 14, 2, 8, 4>; constexpr bool kDelta = true;
 #elif GW_INST == 8
-using C = Cfg<__half, 128, 16, 2, 8, 4>; constexpr bool kDelta = true;
+using C = Cfg<__half, 64, 28, 2, 12, 6>; constexpr bool kDelta = true;
 #elif GW_INST == 9
-using C = Cfg<__nv_bfloat16, 64, 32, 2, 8, 4>;  constexpr bool kDelta = true;
+using C = Cfg<__nv_bfloat16, 64, 28, 2, 8, 4>;  constexpr bool kDelta = true;
 #elif GW_INST == 10
-using C = Cfg<__nv_bfloat16, 64, 16, 2, 8, 4>;  constexpr bool kDelta = true;
+using C = Cfg<__nv_bfloat16, 128, 14, 2, 8, 4>; constexpr bool kDelta = true;
 #elif GW_INST == 11
-using C = Cfg<__nv_bfloat16, 128, 16, 2, 8, 4>; constexpr bool kDelta = true;
+using C = Cfg<__nv_bfloat16, 64, 28, 2, 12, 6>; constexpr bool kDelta = true;
 #else
 #error "unknown configuration index"
 #endif
