@@ -55,46 +55,46 @@ template <class T> struct St;
 template <> struct St<float> {
     using M = float;
     static constexpr int XO = 4;
-    __device__ static void ld4(const float *p, M v[4])
+    __device__ __forceinline__ static void ld4(const float *p, M v[4])
     {
         float4 q = *reinterpret_cast<const float4 *>(p);
         v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
     }
-    __device__ static void st4(float *p, const M v[4])
+    __device__ __forceinline__ static void st4(float *p, const M v[4])
     {
         *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
     }
-    __device__ static void st1(float *p, M v) { *p = v; }
+    __device__ __forceinline__ static void st1(float *p, M v) { *p = v; }
 };
 
 template <> struct St<double> {
     using M = double;
     static constexpr int XO = 4;
-    __device__ static void ld4(const double *p, M v[4])
+    __device__ __forceinline__ static void ld4(const double *p, M v[4])
     {
         double2 a = reinterpret_cast<const double2 *>(p)[0];
         double2 b = reinterpret_cast<const double2 *>(p)[1];
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
-    __device__ static void st4(double *p, const M v[4])
+    __device__ __forceinline__ static void st4(double *p, const M v[4])
     {
         reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
         reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
     }
-    __device__ static void st1(double *p, M v) { *p = v; }
+    __device__ __forceinline__ static void st1(double *p, M v) { *p = v; }
 };
 
 template <> struct St<__half> {
     using M = float;
     static constexpr int XO = 8;
-    __device__ static void ld4(const __half *p, M v[4])
+    __device__ __forceinline__ static void ld4(const __half *p, M v[4])
     {
         uint2 q = *reinterpret_cast<const uint2 *>(p);
         float2 a = __half22float2(*reinterpret_cast<__half2 *>(&q.x));
         float2 b = __half22float2(*reinterpret_cast<__half2 *>(&q.y));
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
-    __device__ static void st4(__half *p, const M v[4])
+    __device__ __forceinline__ static void st4(__half *p, const M v[4])
     {
         __half2 a = __floats2half2_rn(v[0], v[1]);
         __half2 b = __floats2half2_rn(v[2], v[3]);
@@ -103,20 +103,20 @@ template <> struct St<__half> {
         q.y = *reinterpret_cast<uint32_t *>(&b);
         *reinterpret_cast<uint2 *>(p) = q;
     }
-    __device__ static void st1(__half *p, M v) { *p = __float2half_rn(v); }
+    __device__ __forceinline__ static void st1(__half *p, M v) { *p = __float2half_rn(v); }
 };
 
 template <> struct St<__nv_bfloat16> {
     using M = float;
     static constexpr int XO = 8;
-    __device__ static void ld4(const __nv_bfloat16 *p, M v[4])
+    __device__ __forceinline__ static void ld4(const __nv_bfloat16 *p, M v[4])
     {
         uint2 q = *reinterpret_cast<const uint2 *>(p);
         float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&q.x));
         float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&q.y));
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
-    __device__ static void st4(__nv_bfloat16 *p, const M v[4])
+    __device__ __forceinline__ static void st4(__nv_bfloat16 *p, const M v[4])
     {
         __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
         __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
@@ -125,7 +125,7 @@ template <> struct St<__nv_bfloat16> {
         q.y = *reinterpret_cast<uint32_t *>(&b);
         *reinterpret_cast<uint2 *>(p) = q;
     }
-    __device__ static void st1(__nv_bfloat16 *p, M v)
+    __device__ __forceinline__ static void st1(__nv_bfloat16 *p, M v)
     {
         *p = __float2bfloat16_rn(v);
     }
@@ -277,7 +277,7 @@ struct Step {
     __device__ volatile int *abortf() { return misc() + 1; }
     __device__ double *red() { return reinterpret_cast<double *>(smem + C::OFF_RED); }
 
-    __device__ bool wait_or_abort(uint64_t *bar, uint32_t parity)
+    __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity)
     {
         if (aborted) return false;
         if (!wait_slot(bar, parity, abortf())) {
@@ -342,7 +342,7 @@ struct Step {
     }
 
     // ---- item set-up ----------------------------------------------------
-    __device__ void begin_item(int it)
+    __device__ __forceinline__ void begin_item(int it)
     {
         Item I = A.items[it];
         sub = I.sub;
@@ -426,7 +426,7 @@ struct Step {
         nl_ = misc()[0];
     }
 
-    __device__ void end_item(int it)
+    __device__ __forceinline__ void end_item(int it)
     {
         double v = (double)acc + (double)acc2.x + (double)acc2.y;
 #pragma unroll
@@ -619,19 +619,23 @@ struct Step {
 #pragma unroll
             for (int r = 0; r < PY; ++r) laplacian_row(yv, lf[r], rt[r], r, lap[r]);
             const int nl = nl_;
-            // point sources: lap += wavelet[n] at the source cell
-            for (int e = 0; e < nl; ++e) {
-                int4 q = loc()[e];
-                if (q.x < 0 && q.z == z) {
-                    int lx = q.y & 0xffff, ly = q.y >> 16;
-                    if ((lx >> 2) == tx && ly / PY == ty && n < cap_) {
-                        M wv = (M)__ldg(sh->wavelet + (size_t)(-1 - q.x) * cap_ + n);
+            // point sources: lap += wavelet[n] at the source cell (the loop
+            // only finds the point; the add is a select over compile-time
+            // indices, so lap stays in registers)
+            if (nl) {
+                for (int e = 0; e < nl; ++e) {
+                    int4 q = loc()[e];
+                    if (q.x < 0 && q.z == z) {
+                        int lx = q.y & 0xffff, ly = q.y >> 16;
+                        if ((lx >> 2) == tx && ly / PY == ty && n < cap_) {
+                            const int k = (ly % PY) * 4 + (lx & 3);
+                            const M wv = (M)__ldg(sh->wavelet + (size_t)(-1 - q.x) * cap_ + n);
 #pragma unroll
-                        for (int r = 0; r < PY; ++r)
+                            for (int r = 0; r < PY; ++r)
 #pragma unroll
-                            for (int i = 0; i < 4; ++i)
-                                if (r == ly % PY && i == (lx & 3))
-                                    lap[r][i] = add_rn(lap[r][i], wv);
+                                for (int i = 0; i < 4; ++i)
+                                    lap[r][i] = (k == r * 4 + i) ? add_rn(lap[r][i], wv) : lap[r][i];
+                        }
                     }
                 }
             }
@@ -668,18 +672,21 @@ struct Step {
                 if (item_puts) put_halo_row(x0 + 4 * tx, y0 + PY * ty + r, z, so);
             }
             // receivers: trace[n] = u_{n+1}
-            for (int e = 0; e < nl; ++e) {
-                int4 q = loc()[e];
-                if (q.x >= 0 && q.z == z) {
-                    int lx = q.y & 0xffff, ly = q.y >> 16;
-                    if ((lx >> 2) == tx && ly / PY == ty && n < cap_) {
-                        M v = M(0);
+            if (nl) {
+                for (int e = 0; e < nl; ++e) {
+                    int4 q = loc()[e];
+                    if (q.x >= 0 && q.z == z) {
+                        int lx = q.y & 0xffff, ly = q.y >> 16;
+                        if ((lx >> 2) == tx && ly / PY == ty && n < cap_) {
+                            const int k = (ly % PY) * 4 + (lx & 3);
+                            M v = M(0);
 #pragma unroll
-                        for (int r = 0; r < PY; ++r)
+                            for (int r = 0; r < PY; ++r)
 #pragma unroll
-                            for (int i = 0; i < 4; ++i)
-                                if (r == ly % PY && i == (lx & 3)) v = un[r][i];
-                        sh->traces[(size_t)q.x * cap_ + n] = (float)v;
+                                for (int i = 0; i < 4; ++i)
+                                    v = (k == r * 4 + i) ? un[r][i] : v;
+                            sh->traces[(size_t)q.x * cap_ + n] = (float)v;
+                        }
                     }
                 }
             }
@@ -753,7 +760,7 @@ struct Step {
         }
     }
 
-    __device__ void run()
+    __device__ __forceinline__ void run()
     {
         tid = threadIdx.x;
         lane = tid & 31;
