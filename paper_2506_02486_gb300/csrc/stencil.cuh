@@ -151,7 +151,8 @@ template <class M> struct W {
 
 // ---------------------------------------------------------------- config
 
-template <class T_, int TX_, int TY_, int PY_, int SU_, int SP_>
+template <class T_, int TX_, int TY_, int PY_, int SU_, int SP_,
+          int MINB_ = 1, bool PACK_ = true>
 struct Cfg {
     using T = T_;
     using M = typename St<T>::M;
@@ -163,8 +164,10 @@ struct Cfg {
     static constexpr int THREADS = NT + 32;          // + one producer warp
     // registers per thread: each of the SM's 4 sub-partitions owns 16K
     // registers and hosts ceil(warps / 4) of this CTA's warps
+    static constexpr int MINB = MINB_;               // CTAs per SM wanted
+    static constexpr bool PACK = PACK_;              // f32x2 arithmetic
     static constexpr int WPP = (THREADS / 32 + 3) / 4;
-    static constexpr int MAXREG_ = (16384 / (WPP * 32)) / 8 * 8;
+    static constexpr int MAXREG_ = (16384 / (WPP * MINB * 32)) / 8 * 8;
     static constexpr int MAXREG = MAXREG_ > 255 ? 255 : MAXREG_;
     static constexpr int XO = St<T>::XO;
     static constexpr int RW = TX + 2 * XO;          // smem row (elements)
@@ -458,7 +461,7 @@ struct Step {
                 M xp = (i + m <= 3) ? yv[r + R][i + m] : rt[i + m - 4];
                 sx[m][i] = add_rn(xm, xp);
             }
-        if constexpr (std::is_same<M, float>::value) {
+        if constexpr (std::is_same<M, float>::value && C::PACK) {
             const float2 c0 = make_float2(W<M>::c0x3, W<M>::c0x3);
             const float2 c1 = make_float2(W<M>::c1, W<M>::c1);
             const float2 c2 = make_float2(W<M>::c2, W<M>::c2);
@@ -510,7 +513,7 @@ struct Step {
                                                const M (&gxy)[4], M gz, M (&un)[4],
                                                M (&wn)[4])
     {
-        if constexpr (std::is_same<M, float>::value) {
+        if constexpr (std::is_same<M, float>::value && C::PACK) {
 #pragma unroll
             for (int h = 0; h < 4; h += 2) {
                 const float2 U = make_float2(u[h], u[h + 1]);
@@ -560,7 +563,7 @@ struct Step {
     // sum of u'^2 over this thread's valid points (per-lane FP32 partials)
     __device__ __forceinline__ void accumulate_norm(const M (&un)[4])
     {
-        if constexpr (std::is_same<M, float>::value) {
+        if constexpr (std::is_same<M, float>::value && C::PACK) {
             if (vx == 4) {
                 acc2 = __ffma2_rn(make_float2(un[0], un[1]), make_float2(un[0], un[1]), acc2);
                 acc2 = __ffma2_rn(make_float2(un[2], un[3]), make_float2(un[2], un[3]), acc2);

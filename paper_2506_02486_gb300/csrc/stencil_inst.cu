@@ -10,7 +10,8 @@
 
 namespace gw {
 
-// Cfg<storage, tile x, tile y, rows per thread, u-ring slots, pointwise slots>
+// Cfg<storage, tile x, tile y, rows per thread, u-ring slots, pointwise
+//     slots, CTAs per SM wanted, packed f32x2 math>
 #if GW_INST == 0
 using C = Cfg<float, 64, 28, 2, 8, 4>;  constexpr bool kDelta = false;
 #elif GW_INST == 1
@@ -35,6 +36,14 @@ using C = Cfg<__nv_bfloat16, 64, 28, 2, 8, 4>;  constexpr bool kDelta = true;
 using C = Cfg<__nv_bfloat16, 128, 14, 2, 8, 4>; constexpr bool kDelta = true;
 #elif GW_INST == 11
 using C = Cfg<__nv_bfloat16, 64, 28, 2, 12, 6>; constexpr bool kDelta = true;
+#elif GW_INST == 12
+using C = Cfg<float, 64, 28, 2, 8, 4, 1, false>;  constexpr bool kDelta = false;
+#elif GW_INST == 13
+using C = Cfg<float, 64, 14, 1, 8, 4, 2, true>;   constexpr bool kDelta = false;
+#elif GW_INST == 14
+using C = Cfg<float, 128, 7, 1, 8, 4, 2, true>;   constexpr bool kDelta = false;
+#elif GW_INST == 15
+using C = Cfg<__half, 64, 14, 1, 8, 4, 2, true>;  constexpr bool kDelta = true;
 #else
 #error "unknown configuration index"
 #endif
