@@ -205,18 +205,12 @@ void build_items(gw_domain *d)
     }
     int zc = d->desc.zchunk;
     if (zc <= 0) {
-        double best = 1e300;
-        int best_n = 1;
-        for (int nzc = 1; nzc <= std::max(1, nzmax / 4); ++nzc) {
-            long long items = ncols * nzc;
-            long long rounds = (items + d->grid - 1) / d->grid;
-            double cost = (double)rounds * ((double)nzmax / nzc + 8 * 0.3);
-            if (cost < best - 1e-9) {
-                best = cost;
-                best_n = nzc;
-            }
-        }
-        zc = (nzmax + best_n - 1) / best_n;
+        // ~128-plane items (measured on 512^3: deeper items, one per CTA,
+        // and shallower ones both run slower); small grids cut deeper so
+        // that every CTA gets work, down to 32 planes per item
+        int nzc = std::max(1, (nzmax + 127) / 128);
+        while (ncols * nzc < d->grid && nzmax / (nzc + 1) >= 32) ++nzc;
+        zc = (nzmax + nzc - 1) / nzc;
     }
     d->zc = zc;
     struct Key { int z, sub, y, x; };
@@ -304,14 +298,14 @@ gw_status push_shot(gw_domain *d)
 gw_status make_maps(gw_domain *d)
 {
     const int es = d->esize();
-    const int xo = dtype_xoff(d->dtype);
+    const int hl = dtype_halo(d->dtype);
     const bool bf16 = d->dtype == DT_BF16;
     std::vector<CUtensorMap> maps((size_t)d->nsub() * kMapsPerSub);
     std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
     for (int si = 0; si < d->nsub(); ++si) {
         const SubDev &s = d->subs[si];
         CUtensorMap *m = &maps[(size_t)si * kMapsPerSub];
-        int hx = d->ti.tx + 2 * xo, hy = d->ti.ty + 2 * R;
+        int hx = d->ti.tx + 2 * hl, hy = d->ti.ty + 2 * R;
         GW_TRY(encode_map(d, &m[MAP_U0_HALO], s.u[0], s, es, bf16, hx, hy));
         GW_TRY(encode_map(d, &m[MAP_U1_HALO], s.u[1], s, es, bf16, hx, hy));
         GW_TRY(encode_map(d, &m[MAP_U0_PW], s.u[0], s, es, bf16, d->ti.tx, d->ti.ty));

@@ -10,8 +10,10 @@ namespace gw {
 enum Dtype { DT_F32 = 0, DT_F64 = 1, DT_F16S = 2, DT_BF16 = 3 };
 
 inline int dtype_size(int dt) { return dt == DT_F64 ? 8 : dt == DT_F32 ? 4 : 2; }
-// Interior x offset in a padded row: >= R and 16-byte aligned.
-inline int dtype_xoff(int dt) { return dtype_size(dt) == 2 ? 8 : 4; }
+// Interior x offset in a padded row: >= R and 32-byte (sector) aligned.
+inline int dtype_xoff(int dt) { return dtype_size(dt) == 2 ? 16 : dtype_size(dt) == 4 ? 8 : 4; }
+// x halo staged in shared memory: >= R and a multiple of 16 bytes.
+inline int dtype_halo(int dt) { return dtype_size(dt) == 2 ? 8 : 4; }
 
 struct TileInfo {
     int tx, ty;        // tile extent in x and y (interior points)

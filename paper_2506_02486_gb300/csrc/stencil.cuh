@@ -52,9 +52,13 @@ namespace gw {
 
 template <class T> struct St;
 
+// XO: x offset of the interior in a padded global row (32-byte aligned, so
+// rows of a tile are written and read in whole sectors); HL: x halo staged
+// in shared memory (>= R and a multiple of 16 bytes, a TMA requirement on
+// the box's first coordinate).
 template <> struct St<float> {
     using M = float;
-    static constexpr int XO = 4;
+    static constexpr int XO = 8, HL = 4;
     __device__ __forceinline__ static void ld4(const float *p, M v[4])
     {
         float4 q = *reinterpret_cast<const float4 *>(p);
@@ -69,7 +73,7 @@ template <> struct St<float> {
 
 template <> struct St<double> {
     using M = double;
-    static constexpr int XO = 4;
+    static constexpr int XO = 4, HL = 4;
     __device__ __forceinline__ static void ld4(const double *p, M v[4])
     {
         double2 a = reinterpret_cast<const double2 *>(p)[0];
@@ -86,7 +90,7 @@ template <> struct St<double> {
 
 template <> struct St<__half> {
     using M = float;
-    static constexpr int XO = 8;
+    static constexpr int XO = 16, HL = 8;
     __device__ __forceinline__ static void ld4(const __half *p, M v[4])
     {
         uint2 q = *reinterpret_cast<const uint2 *>(p);
@@ -108,7 +112,7 @@ template <> struct St<__half> {
 
 template <> struct St<__nv_bfloat16> {
     using M = float;
-    static constexpr int XO = 8;
+    static constexpr int XO = 16, HL = 8;
     __device__ __forceinline__ static void ld4(const __nv_bfloat16 *p, M v[4])
     {
         uint2 q = *reinterpret_cast<const uint2 *>(p);
@@ -170,7 +174,8 @@ struct Cfg {
     static constexpr int MAXREG_ = (16384 / (WPP * MINB * 32)) / 8 * 8;
     static constexpr int MAXREG = MAXREG_ > 255 ? 255 : MAXREG_;
     static constexpr int XO = St<T>::XO;
-    static constexpr int RW = TX + 2 * XO;          // smem row (elements)
+    static constexpr int HL = St<T>::HL;
+    static constexpr int RW = TX + 2 * HL;          // smem row (elements)
     static constexpr int UROWS = TY + 2 * R;
     static constexpr int UBYTES = RW * UROWS * (int)sizeof(T);
     static constexpr int PBYTES = TX * TY * (int)sizeof(T);
@@ -224,7 +229,7 @@ struct Step {
     using M = typename C::M;
     using S = St<T>;
     static constexpr int TX = C::TX, TY = C::TY, PY = C::PY;
-    static constexpr int SU = C::SU, SP = C::SP, XO = C::XO;
+    static constexpr int SU = C::SU, SP = C::SP, XO = C::XO, HL = C::HL;
 
     const StepArgs &A;
     unsigned char *smem;
@@ -310,7 +315,9 @@ struct Step {
             tensormap_acquire(map_u);
             tensormap_acquire(map_a);
             tensormap_acquire(map_b);
-            const int ux = I.xy & 0xffff, uy = I.xy >> 16;   // padded box origin
+            // padded coordinates of the boxes: interior (x0 - HL, y0 - R)
+            // for the halo box, (x0, y0) for the pointwise tiles
+            const int ux = (I.xy & 0xffff) + XO - HL, uy = I.xy >> 16;
             const int T = I.z1 - I.z0 + 2 * R;
             for (int t = 0; t < T; ++t) {
                 unsigned slot = L % SU;
@@ -329,8 +336,8 @@ struct Step {
                     }
                     mbar_arrive_expect_tx(pfull(ps), 2 * C::PBYTES);
                     const int zz = I.z0 + t - R;   // padded z of interior z
-                    tma_load_3d(pbuf(ps, 0), map_a, pfull(ps), ux + XO, uy + R, zz, pol_first);
-                    tma_load_3d(pbuf(ps, 1), map_b, pfull(ps), ux + XO, uy + R, zz, pol_first);
+                    tma_load_3d(pbuf(ps, 0), map_a, pfull(ps), ux + HL, uy + R, zz, pol_first);
+                    tma_load_3d(pbuf(ps, 1), map_b, pfull(ps), ux + HL, uy + R, zz, pol_first);
                     ++P;
                 }
             }
@@ -589,7 +596,7 @@ struct Step {
             const T *pl = ubuf(slot);
 #pragma unroll
             for (int r = 0; r < PY; ++r)
-                S::ld4(pl + (PY * ty + r + R) * C::RW + XO + 4 * tx, Q[8][r]);
+                S::ld4(pl + (PY * ty + r + R) * C::RW + HL + 4 * tx, Q[8][r]);
         }
         // (2) compute plane z = z0 + t - 8 once the queue is full
         if (t >= 2 * R) {
@@ -600,11 +607,11 @@ struct Step {
             M yv[PY + 8][4];
 #pragma unroll
             for (int j = 0; j < PY + 8; ++j)
-                S::ld4(pl + (PY * ty + j) * C::RW + XO + 4 * tx, yv[j]);
+                S::ld4(pl + (PY * ty + j) * C::RW + HL + 4 * tx, yv[j]);
             M lf[PY][4], rt[PY][4], pa[PY][4], cf[PY][4];
 #pragma unroll
             for (int r = 0; r < PY; ++r) {
-                const T *row = pl + (PY * ty + r + R) * C::RW + XO + 4 * tx;
+                const T *row = pl + (PY * ty + r + R) * C::RW + HL + 4 * tx;
                 S::ld4(row - 4, lf[r]);
                 S::ld4(row + 4, rt[r]);
                 S::ld4(pbuf(ps, 0) + (PY * ty + r) * TX + 4 * tx, pa[r]);

@@ -43,7 +43,7 @@ class Segment:
 def padded_bytes(nx: int, ny: int, nz: int, dtype: str = "f32") -> int:
     """Bytes of one padded field array (x pitch a multiple of 128 bytes)."""
     es = {"f32": 4, "f64": 8, "f16s": 2, "bf16": 2}[dtype]
-    xo = 8 if es == 2 else 4
+    xo = {2: 16, 4: 8, 8: 4}[es]
     mul = 128 // es
     px = -(-(xo + nx + 4) // mul) * mul
     return px * (ny + 8) * (nz + 8) * es

@@ -90,7 +90,7 @@ def read_padded(host, base, shot, rank, snx, sny, snz, symmetric, sx, sz):
     # (symmetric: offset 0 on every rank; asymmetric: top of each rank)
     lx = max(sx) if symmetric else snx
     ly = sny
-    px = -(-(4 + lx + 4) // 32) * 32
+    px = -(-(8 + lx + 4) // 32) * 32      # FP32: interior at x offset 8
     py = ly + 8
     pzp = (max(sz) if symmetric else snz) + 8
     nbytes = px * py * pzp * 4
@@ -99,4 +99,4 @@ def read_padded(host, base, shot, rank, snx, sny, snz, symmetric, sx, sz):
     else:
         off = rank * rank_bytes + rank_bytes - (-(-nbytes // 256) * 256)
     arr = host[off:off + nbytes].view(np.float32).reshape(pzp, py, px)
-    return arr[:snz + 8, :sny + 8, 0:snx + 8].astype(np.float64)
+    return arr[:snz + 8, :sny + 8, 4:snx + 12].astype(np.float64)
