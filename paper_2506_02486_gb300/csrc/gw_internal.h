@@ -10,7 +10,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/gbwave.h"
+#include "gbwave.h"
 #include "gw_device.h"
 #include "gw_kernels.h"
 
