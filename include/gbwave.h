@@ -280,6 +280,36 @@ gw_status gw_norms(gw_domain *d, double *host_out, int n);
  * Synchronises; GW_ERR_NUMERIC if non-finite. */
 gw_status gw_check(gw_domain *d, double *norm2, double *energy);
 
+/* Allocation-free variant of gw_check, for callers that cannot allocate
+ * device memory (code running while another framework holds its memory
+ * pool, an embedded runtime that owns all device memory, a latency-critical
+ * path that must not wait on an allocation).  The paper has no counterpart;
+ * it is a library convenience.
+ *
+ * u_cur, u_prev, coef: device arrays of one grid in the library's padded
+ * layout (element (x, y, z) at ((z + 4) * (ny + 8) + (y + 4)) * px + xoff +
+ * x, xoff = 8 for GW_F32, 4 for GW_F64, 16 for GW_F16S / GW_BF16; coef is
+ * FP16 for the two 16-bit types), halo cells holding the boundary values
+ * (zero for a zero boundary).  px: row pitch in elements, >= xoff + nx + 4.
+ * scale_u: the power-of-two scale the u arrays are stored with (1 unless
+ * GW_F16S).  out_dev: 3 doubles of device memory that receive
+ * sum u^2, sum (u - u_prev)^2 / coef and sum u lap(u_prev); the energy of
+ * gw_check is out_dev[1] - out_dev[2].  Enqueued on `stream`, no host sync.
+ *
+ * The per-plane partial sums live in one built-in device array of
+ * 4096 x 3 doubles (96 KiB) that every GPU which loads the library keeps
+ * until the process exits: nz > 4096 is rejected with GW_ERR_ARG.  The first
+ * call on a device looks up that array's device address (with the device
+ * current), so make the first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (different streams, no
+ * ordering between them) race; calls ordered on one stream do not.  Each
+ * call overwrites the partials it uses, so nothing needs clearing.
+ * Calls no cudaMalloc, cudaFree or allocating library routine. */
+gw_status gw_check_fields_noalloc(const void *u_cur, const void *u_prev,
+                                  const void *coef, int dtype, int nx, int ny,
+                                  int nz, int px, double scale_u,
+                                  double *out_dev, gw_stream stream);
+
 /* Record the device time of every step-kernel launch (CUDA events) while
  * enabled; gw_kernel_stats_get returns the totals and resets them. */
 gw_status gw_kernel_timing(gw_domain *d, int enable);

@@ -113,6 +113,7 @@ _SIGS = {
     "gw_write_wavefield": [_P, _I, _P, _I],
     "gw_norms": [_P, _P, _I],
     "gw_check": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "gw_check_fields_noalloc": [_P, _P, _P, _I, _I, _I, _I, _I, _D, _P, _P],
     "gw_kernel_timing": [_P, _I],
     "gw_kernel_stats_get": [_P, ctypes.POINTER(gw_kernel_stats)],
     "gw_state_bytes": [_P, ctypes.POINTER(_SZ)],
@@ -399,6 +400,16 @@ def gw_check(dom: int) -> tuple[float, float]:
     a, b = _D(), _D()
     _check(lib().gw_check(dom, ctypes.byref(a), ctypes.byref(b)), "gw_check")
     return a.value, b.value
+
+
+def gw_check_fields_noalloc(u_cur, u_prev, coef, dtype, nx: int, ny: int,
+                            nz: int, px: int, scale_u: float, out_dev,
+                            stream=None):
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    _check(lib().gw_check_fields_noalloc(
+        _ptr(u_cur), _ptr(u_prev), _ptr(coef), dt, int(nx), int(ny), int(nz),
+        int(px), float(scale_u), _ptr(out_dev), _stream(stream)),
+        "gw_check_fields_noalloc")
 
 
 def gw_kernel_timing(dom: int, enable: bool):
