@@ -425,6 +425,30 @@ def run_ours(args, world, rank, local, pg):
     return 0
 
 
+def run_case(args):
+    """One plain shot of an N^3 layered model (no timing extras): the
+    workload the ncu captures profile."""
+    import workloads
+    from paper_2506_02486_gb300 import buildlib
+    from paper_2506_02486_gb300.runtime import Segment, Shot, padded_bytes
+    buildlib.build()
+    n = args.case
+    shot = workloads.layered_cube(n)
+    with Segment(4 * padded_bytes(n, n, n, args.dtype) + (512 << 20)) as seg:
+        with Shot(seg, n, n, n, nsteps=args.steps, sponge=shot.sponge,
+                  dtype=args.dtype, chunk=-1) as s:
+            s.set_model(shot.vel)
+            s.add_ricker(shot.src, shot.f_peak)
+            s.set_receivers(shot.receivers)
+            s.step(args.steps)
+            s.sync()
+            info = s.info
+    print(json.dumps({"case": n, "dtype": args.dtype, "steps": args.steps,
+                      "tile": info["tile"], "ctas": info["ctas"],
+                      "items": info["items"]}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,7 +458,12 @@ def main():
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline",
                     action="store_false")
+    ap.add_argument("--case", type=int, default=0,
+                    help="run one plain N^3 shot for --steps steps (profiling)")
+    ap.add_argument("--dtype", default="f32", help="storage type for --case")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
