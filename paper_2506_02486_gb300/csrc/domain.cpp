@@ -205,12 +205,24 @@ void build_items(gw_domain *d)
     }
     int zc = d->desc.zchunk;
     if (zc <= 0) {
-        // ~128-plane items (measured on 512^3: deeper items, one per CTA,
-        // and shallower ones both run slower); small grids cut deeper so
-        // that every CTA gets work, down to 32 planes per item
-        int nzc = std::max(1, (nzmax + 127) / 128);
-        while (ncols * nzc < d->grid && nzmax / (nzc + 1) >= 32) ++nzc;
-        zc = (nzmax + nzc - 1) / nzc;
+        // Items of at most 128 planes (measured on 512^3: one item per CTA
+        // and 32-plane items both run slower), chosen to fill the last
+        // round of `grid` CTAs: cost = rounds * (planes + 8 * alpha), where
+        // a streamed-only halo plane costs alpha = 0.5 of a computed one.
+        double best = 1e300;
+        int best_n = 1;
+        const int lo = std::max(1, (nzmax + 127) / 128);
+        const int hi = std::max(lo, nzmax / 32);
+        for (int nzc = lo; nzc <= hi; ++nzc) {
+            long long items = ncols * nzc;
+            long long rounds = (items + d->grid - 1) / d->grid;
+            double cost = (double)rounds * ((double)nzmax / nzc + 8 * 0.5);
+            if (cost < best - 1e-9) {
+                best = cost;
+                best_n = nzc;
+            }
+        }
+        zc = (nzmax + best_n - 1) / best_n;
     }
     d->zc = zc;
     struct Key { int z, sub, y, x; };

@@ -187,7 +187,8 @@ struct Cfg {
     static constexpr int OFF_LOC = OFF_BAR + 16 * (SU + SP);   // full + empty
     static constexpr int OFF_MISC = OFF_LOC + 16 * kMaxLocal;
     static constexpr int OFF_RED = OFF_MISC + 16;
-    static constexpr int SMEM = OFF_RED + 8 * NCW;
+    static constexpr int OFF_NBR = OFF_RED + 8 * NCW;     // 6 x NbrPut (32 B)
+    static constexpr int SMEM = OFF_NBR + 32 * 6;
     static_assert(TX % 4 == 0 && TY % PY == 0 && NT % 32 == 0, "tile");
     static_assert((RW * (int)sizeof(T)) % 16 == 0, "TMA box row");
     static_assert(SU >= 6 && SP >= 2, "ring depth");
@@ -222,6 +223,19 @@ __device__ __forceinline__ void consumer_sync(int nthreads)
 }
 
 // ---------------------------------------------------------------- kernel
+
+// Where the fused halo puts of the current item go, per face: the
+// neighbour's buffer receiving u_{n+1} and its strides, resolved once per
+// item (symmetric: own buffer + rank distance x rank stride; asymmetric: the
+// resolved second-level pointer) and kept in shared memory.
+struct NbrPut {
+    char *base;            // neighbour's u_{n+1} buffer (nullptr: no neighbour)
+    long long plane;       // elements per plane
+    int px;                // row pitch (elements)
+    int ext;               // neighbour extent along the face normal
+    int pad_[2];
+};
+static_assert(sizeof(NbrPut) == 32, "NbrPut size");
 
 template <class C, bool DELTA, bool SPONGE>
 struct Step {
@@ -284,6 +298,7 @@ struct Step {
     __device__ int *misc() { return reinterpret_cast<int *>(smem + C::OFF_MISC); }
     __device__ volatile int *abortf() { return misc() + 1; }
     __device__ double *red() { return reinterpret_cast<double *>(smem + C::OFF_RED); }
+    __device__ NbrPut *nbrput() { return reinterpret_cast<NbrPut *>(smem + C::OFF_NBR); }
 
     __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity)
     {
@@ -431,6 +446,23 @@ struct Step {
                 }
             }
             if (lane == 0) misc()[0] = min(cnt, kMaxLocal);
+        }
+        if (tid == 32 && item_puts) {
+            for (int f = 0; f < 6; ++f) {
+                NbrPut q{};
+                const int nb = nbr_[f];
+                if (nb >= 0) {
+                    const SubDev &o = A.subs[nb];
+                    q.base = A.symmetric
+                                 ? reinterpret_cast<char *>(unext) +
+                                       (long long)(o.rank - rank_) * A.rank_stride
+                                 : o.u[par ^ 1];
+                    q.plane = (long long)o.px * o.py;
+                    q.px = o.px;
+                    q.ext = (f >> 1) == 0 ? o.nx : (f >> 1) == 1 ? o.ny : o.nz;
+                }
+                nbrput()[f] = q;
+            }
         }
         consumer_sync(C::NT);
         nl_ = misc()[0];
@@ -721,20 +753,16 @@ struct Step {
 
     // One-sided puts of a freshly computed row segment into the halos of
     // the face neighbours that read it (Listing 1's ompx_put, fused).
-    // mask selects which of the 4 points to store; all4 stores one vector.
-    __device__ __forceinline__ void put_row(int nb, int x, int y, int z, const M (&so)[4],
-                            unsigned mask, bool all4)
+    // mask selects which of the 4 points to store; a full, 16-byte aligned
+    // segment is stored as one vector.
+    __device__ __forceinline__ void put_row(int f, int x, int y, int z,
+                                            const M (&so)[4], unsigned mask)
     {
-        const SubDev &o = A.subs[nb];
-        T *base;
-        if (A.symmetric)
-            base = reinterpret_cast<T *>(
-                reinterpret_cast<char *>(unext) +
-                (long long)(o.rank - rank_) * A.rank_stride);
-        else
-            base = reinterpret_cast<T *>(o.u[par ^ 1]);
-        const size_t off = ((size_t)(z + R) * o.py + (size_t)(y + R)) * o.px + XO + x;
-        if (all4) {
+        const NbrPut q = nbrput()[f];
+        T *base = reinterpret_cast<T *>(q.base);
+        const long long off = (long long)(z + R) * q.plane +
+                              (long long)(y + R) * q.px + XO + x;
+        if (mask == 0xFu && ((XO + x) & 3) == 0) {
             S::st4(base + off, so);
         } else {
 #pragma unroll
@@ -745,28 +773,27 @@ struct Step {
 
     __device__ __forceinline__ void put_halo_row(int x, int y, int z, const M (&so)[4])
     {
-        const bool all4 = vx == 4;
         const unsigned valid = (1u << vx) - 1u;
         if (z < R && nbr_[4] >= 0)
-            put_row(nbr_[4], x, y, A.subs[nbr_[4]].nz + z, so, valid, all4);
+            put_row(4, x, y, nbrput()[4].ext + z, so, valid);
         if (z >= nz - R && nbr_[5] >= 0)
-            put_row(nbr_[5], x, y, z - nz, so, valid, all4);
+            put_row(5, x, y, z - nz, so, valid);
         if (y < R && nbr_[2] >= 0)
-            put_row(nbr_[2], x, A.subs[nbr_[2]].ny + y, z, so, valid, all4);
+            put_row(2, x, nbrput()[2].ext + y, z, so, valid);
         if (y >= ny - R && nbr_[3] >= 0)
-            put_row(nbr_[3], x, y - ny, z, so, valid, all4);
+            put_row(3, x, y - ny, z, so, valid);
         if (x < R && nbr_[0] >= 0) {
             // points x + i < R go to the -x neighbour's +x halo
             unsigned m = 0;
 #pragma unroll
             for (int i = 0; i < 4; ++i) m |= (x + i < R ? 1u : 0u) << i;
-            put_row(nbr_[0], A.subs[nbr_[0]].nx + x, y, z, so, m & valid, false);
+            put_row(0, nbrput()[0].ext + x, y, z, so, m & valid);
         }
         if (x + vx > nx - R && nbr_[1] >= 0) {
             unsigned m = 0;
 #pragma unroll
             for (int i = 0; i < 4; ++i) m |= (x + i >= nx - R ? 1u : 0u) << i;
-            put_row(nbr_[1], x - nx, y, z, so, m & valid, false);
+            put_row(1, x - nx, y, z, so, m & valid);
         }
     }
 
