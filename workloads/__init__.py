@@ -230,14 +230,27 @@ def layered_cube(n: int = 512, seed: int = 2506, nsteps: int = 1000,
 
 def perturbed_box(nx: int = 1024, ny: int = 1024, nz: int = 512,
                   seed: int = 2507, nsteps: int = 500, sponge: int = 20,
-                  vel_dtype=np.float32) -> ShotInputs:
+                  vel_dtype=np.float32, crop=None) -> ShotInputs:
     """The layered model with 5% i.i.d. Gaussian perturbations (clipped at
-    20%) on an nx x ny x nz grid; 20 Hz source at a seeded cell."""
-    base = np.empty((nz, ny, nx), dtype=vel_dtype)
+    20%) on an nx x ny x nz grid; 20 Hz source at a seeded cell.
+
+    crop = (cx, cy, cz) returns the corner [0, cx) x [0, cy) x [0, cz) of
+    exactly that model (the same layers and the same per-cell draws), with
+    the source at the centre of the crop."""
     rng = np.random.default_rng(seed)
-    base[...] = _layer_profile(nz, rng, 8, 1500.0, 4500.0)[:, None, None]
-    vel = perturbed(base, seed + 1, out_dtype=vel_dtype)
-    src = source_position(seed + 2, nx, ny, nz, margin=sponge)
-    rec = lattice_receivers(nx, ny, sponge, n=8, margin=sponge)
-    return ShotInputs(f"perturbed_{nx}x{ny}x{nz}", vel, src, rec, 20.0,
+    prof = _layer_profile(nz, rng, 8, 1500.0, 4500.0)
+    cx, cy, cz = (nx, ny, nz) if crop is None else crop
+    base = np.empty((cz, cy, cx), dtype=vel_dtype)
+    pr = np.random.default_rng(seed + 1)
+    for k in range(cz):
+        eps = pr.standard_normal((ny, nx)) * 0.05
+        np.clip(eps, -0.2, 0.2, out=eps)
+        base[k] = prof[k] * (1.0 + eps[:cy, :cx])
+    if crop is None:
+        src = source_position(seed + 2, nx, ny, nz, margin=sponge)
+        rec = lattice_receivers(nx, ny, sponge, n=8, margin=sponge)
+    else:
+        src = (cx // 2, cy // 2, cz // 2)
+        rec = lattice_receivers(cx, cy, sponge, n=8, margin=sponge)
+    return ShotInputs(f"perturbed_{cx}x{cy}x{cz}", base, src, rec, 20.0,
                       nsteps, sponge)
