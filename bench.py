@@ -449,6 +449,57 @@ def run_case(args):
     return 0
 
 
+def run_precision(args):
+    """Storage types on the 1024 x 1024 x 512 perturbed layered model, 500
+    steps: Gpts/s of each and its error against the FP64 GPU path (whose
+    agreement with the oracle is pinned on a 128^3 crop by the tests)."""
+    import torch
+    import workloads
+    from paper_2506_02486_gb300 import buildlib
+    from paper_2506_02486_gb300 import gbwave as gw
+    from paper_2506_02486_gb300.runtime import Segment, Shot, padded_bytes
+    buildlib.build()
+    shot = workloads.perturbed_box()
+    nz, ny, nx = shot.vel.shape
+    steps = args.steps if args.steps != 1000 else shot.nsteps
+    npts = nx * ny * nz
+    res, ref = {}, None
+    for dt in ("f64", "f32", "f16s", "bf16"):
+        nf = 4 if dt in ("f16s", "bf16") else 3
+        with Segment(nf * padded_bytes(nx, ny, nz, dt) + (1 << 30)) as seg:
+            with Shot(seg, nx, ny, nz, nsteps=steps, dtype=dt,
+                      sponge=shot.sponge) as s:
+                gw.gw_set_model_f32(s.dom, shot.vel)
+                s.add_ricker(shot.src, shot.f_peak)
+                s.set_receivers(shot.receivers)
+                s.sync()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                s.step(steps)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                u = s.u(f64=True)
+                info = s.info
+        r = {"gpts": npts * steps / (ms * 1e-3) / 1e9, "ms": ms,
+             "scale_u": info["scale_u"]}
+        if ref is None:
+            ref = (u,)
+        else:
+            d = u - ref[0]
+            r["rel_l2"] = float(np.linalg.norm(d) / np.linalg.norm(ref[0]))
+            r["max_abs"] = float(np.abs(d).max())
+        res[dt] = r
+        del u
+    res["max_abs_u"] = float(np.abs(ref[0]).max())
+    for dt in ("f16s", "bf16"):
+        res[dt]["speedup_vs_f32"] = res[dt]["gpts"] / res["f32"]["gpts"]
+    print(json.dumps({"precision": shot.name, "steps": steps,
+                      "sponge": shot.sponge, "results": res}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -461,9 +512,13 @@ def main():
     ap.add_argument("--case", type=int, default=0,
                     help="run one plain N^3 shot for --steps steps (profiling)")
     ap.add_argument("--dtype", default="f32", help="storage type for --case")
+    ap.add_argument("--precision", action="store_true",
+                    help="storage types vs FP64 on the 1024x1024x512 model")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
+    if args.precision:
+        return run_precision(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
