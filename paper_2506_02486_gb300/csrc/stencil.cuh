@@ -222,6 +222,61 @@ __device__ __forceinline__ void consumer_sync(int nthreads)
     asm volatile("bar.sync 1, %0;" :: "r"(nthreads) : "memory");
 }
 
+// ---------------------------------------------------------------- groups
+
+// Four consecutive x points of one row.  For packed FP32 arithmetic they
+// are held as two float2 pairs, so packed operands are always aligned
+// register pairs and never need moving; otherwise as four scalars.
+template <class M, bool P> struct Grp {
+    M v[4];
+    __device__ __forceinline__ M get(int i) const { return v[i]; }
+    __device__ __forceinline__ void set(int i, M x) { v[i] = x; }
+};
+template <> struct Grp<float, true> {
+    float2 a, b;
+    __device__ __forceinline__ float get(int i) const
+    {
+        return i == 0 ? a.x : i == 1 ? a.y : i == 2 ? b.x : b.y;
+    }
+    __device__ __forceinline__ void set(int i, float x)
+    {
+        if (i == 0) a.x = x; else if (i == 1) a.y = x; else if (i == 2) b.x = x; else b.y = x;
+    }
+    __device__ __forceinline__ float2 pair(int h) const { return h ? b : a; }
+};
+
+// Load a group of storage type T from shared memory.
+template <class T, bool P>
+__device__ __forceinline__ void ld_grp(const T *p, Grp<typename St<T>::M, P> &g)
+{
+    typename St<T>::M v[4];
+    St<T>::ld4(p, v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) g.set(i, v[i]);
+}
+template <>
+__device__ __forceinline__ void ld_grp<float, true>(const float *p, Grp<float, true> &g)
+{
+    float4 q = *reinterpret_cast<const float4 *>(p);
+    g.a = make_float2(q.x, q.y);
+    g.b = make_float2(q.z, q.w);
+}
+template <>
+__device__ __forceinline__ void ld_grp<__half, true>(const __half *p, Grp<float, true> &g)
+{
+    uint2 q = *reinterpret_cast<const uint2 *>(p);
+    g.a = __half22float2(*reinterpret_cast<__half2 *>(&q.x));
+    g.b = __half22float2(*reinterpret_cast<__half2 *>(&q.y));
+}
+template <>
+__device__ __forceinline__ void ld_grp<__nv_bfloat16, true>(const __nv_bfloat16 *p,
+                                                           Grp<float, true> &g)
+{
+    uint2 q = *reinterpret_cast<const uint2 *>(p);
+    g.a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&q.x));
+    g.b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&q.y));
+}
+
 // ---------------------------------------------------------------- kernel
 
 // Where the fused halo puts of the current item go, per face: the
@@ -273,10 +328,16 @@ struct Step {
     const SubDev *sd;
     const ShotDev *sh;
     T *unext, *wbuf;
-    M gxy[PY][4];
+    // packed FP32 arithmetic on float2 pairs (Blackwell f32x2 add/mul/fma)
+    static constexpr bool PK = std::is_same<M, float>::value && C::PACK;
+    using G = Grp<M, PK>;
+    // planes per trip of the z loop: the register queue shifts by KP planes
+    // once per trip (KP planes of phases share one shift)
+    static constexpr int KP = 2;
+    G gxy[PY];                 // g_x g_y of this thread's points
     M acc;
     float2 acc2;               // packed FP32 norm partials
-    M Q[9][PY][4];
+    G Q[8 + KP][PY];           // this thread's points on planes z-4 .. z+4+KP-1
 
     __device__ Step(const StepArgs &a, unsigned char *sm) : A(a), smem(sm) {}
 
@@ -411,7 +472,7 @@ struct Step {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     int gx = min(sd->gx0 + xs + i, sh->NX - 1);
-                    gxy[r][i] = mul_rn((M)__ldg(sh->gx + gx), fy);
+                    gxy[r].set(i, mul_rn((M)__ldg(sh->gx + gx), fy));
                 }
             }
         }
@@ -483,49 +544,47 @@ struct Step {
     }
 
     // ---- arithmetic of one row of 4 points ---------------------------
-    // FP32 math runs on packed pairs (Blackwell f32x2 add/mul/fma, each lane
-    // rounded once to nearest: the same bits as the scalar order below).
-    // The x pair sums stay scalar so that no operand needs re-pairing.
-    __device__ __forceinline__ void laplacian_row(const M (&yv)[PY + 8][4],
-                                                  const M (&lf)[4],
-                                                  const M (&rt)[4], int r,
-                                                  M (&out)[4])
+    // P is the plane's phase within a trip of the z loop: its z neighbours
+    // sit at queue entries R + P - m and R + P + m.  Pair sums along x stay
+    // scalar (their operands straddle the pairs); with PK everything else
+    // runs on aligned float2 pairs, each lane rounded once to nearest, which
+    // gives the same bits as the scalar order.
+    template <int P>
+    __device__ __forceinline__ void laplacian_row(const G (&yv)[PY + 8], const G &lf,
+                                                  const G &rt, int r, G &out)
     {
+        constexpr int c = R + P;
         M sx[5][4];
 #pragma unroll
         for (int m = 1; m <= 4; ++m)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                M xm = (i - m >= 0) ? yv[r + R][i - m] : lf[4 + i - m];
-                M xp = (i + m <= 3) ? yv[r + R][i + m] : rt[i + m - 4];
+                M xm = (i - m >= 0) ? yv[r + R].get(i - m) : lf.get(4 + i - m);
+                M xp = (i + m <= 3) ? yv[r + R].get(i + m) : rt.get(i + m - 4);
                 sx[m][i] = add_rn(xm, xp);
             }
-        if constexpr (std::is_same<M, float>::value && C::PACK) {
+        if constexpr (PK) {
             const float2 c0 = make_float2(W<M>::c0x3, W<M>::c0x3);
             const float2 c1 = make_float2(W<M>::c1, W<M>::c1);
             const float2 c2 = make_float2(W<M>::c2, W<M>::c2);
             const float2 c3 = make_float2(W<M>::c3, W<M>::c3);
             const float2 c4 = make_float2(W<M>::c4, W<M>::c4);
 #pragma unroll
-            for (int h = 0; h < 4; h += 2) {
+            for (int h = 0; h < 2; ++h) {
                 float2 S[5];
 #pragma unroll
                 for (int m = 1; m <= 4; ++m) {
-                    float2 sy = __fadd2_rn(make_float2(yv[r + R - m][h], yv[r + R - m][h + 1]),
-                                           make_float2(yv[r + R + m][h], yv[r + R + m][h + 1]));
-                    float2 sz = __fadd2_rn(make_float2(Q[R - m][r][h], Q[R - m][r][h + 1]),
-                                           make_float2(Q[R + m][r][h], Q[R + m][r][h + 1]));
-                    S[m] = __fadd2_rn(__fadd2_rn(make_float2(sx[m][h], sx[m][h + 1]), sy), sz);
+                    float2 sy = __fadd2_rn(yv[r + R - m].pair(h), yv[r + R + m].pair(h));
+                    float2 sz = __fadd2_rn(Q[c - m][r].pair(h), Q[c + m][r].pair(h));
+                    S[m] = __fadd2_rn(__fadd2_rn(make_float2(sx[m][2 * h], sx[m][2 * h + 1]), sy), sz);
                 }
-                float2 c = make_float2(yv[r + R][h], yv[r + R][h + 1]);
-                float2 l = __ffma2_rn(c1, S[1], __fmul2_rn(c0, c));
+                float2 l = __ffma2_rn(c1, S[1], __fmul2_rn(c0, yv[r + R].pair(h)));
                 l = __ffma2_rn(c2, S[2], l);
                 l = __ffma2_rn(c3, S[3], l);
                 l = __ffma2_rn(c4, S[4], l);
                 // delta storage holds su * u: undo the power-of-two scale
                 if (DELTA) l = __fmul2_rn(l, make_float2(isu_, isu_));
-                out[h] = l.x;
-                out[h + 1] = l.y;
+                if (h) out.b = l; else out.a = l;
             }
         } else {
 #pragma unroll
@@ -533,92 +592,90 @@ struct Step {
                 M s[5];
 #pragma unroll
                 for (int m = 1; m <= 4; ++m)
-                    s[m] = add_rn(add_rn(sx[m][i], add_rn(yv[r + R - m][i], yv[r + R + m][i])),
-                                  add_rn(Q[R - m][r][i], Q[R + m][r][i]));
-                M l = fma_rn(W<M>::c1, s[1], mul_rn(W<M>::c0x3, yv[r + R][i]));
+                    s[m] = add_rn(add_rn(sx[m][i], add_rn(yv[r + R - m].get(i), yv[r + R + m].get(i))),
+                                  add_rn(Q[c - m][r].get(i), Q[c + m][r].get(i)));
+                M l = fma_rn(W<M>::c1, s[1], mul_rn(W<M>::c0x3, yv[r + R].get(i)));
                 l = fma_rn(W<M>::c2, s[2], l);
                 l = fma_rn(W<M>::c3, s[3], l);
                 l = fma_rn(W<M>::c4, s[4], l);
                 if (DELTA) l = mul_rn(l, isu_);
-                out[i] = l;
+                out.set(i, l);
             }
         }
     }
 
     // 3-level: u' = G (2u - G u_prev + coef lap);
     // delta:   w' = G (w + coef lap),  u' = G u + w'.
-    __device__ __forceinline__ void update_row(const M (&u)[4], const M (&pa)[4],
-                                               const M (&cf)[4], const M (&lap)[4],
-                                               const M (&gxy)[4], M gz, M (&un)[4],
-                                               M (&wn)[4])
+    __device__ __forceinline__ void update_row(const G &u, const G &pa, const G &cf,
+                                               const G &lap, const G &gxy, M gz,
+                                               G &un, G &wn)
     {
-        if constexpr (std::is_same<M, float>::value && C::PACK) {
+        if constexpr (PK) {
 #pragma unroll
-            for (int h = 0; h < 4; h += 2) {
-                const float2 U = make_float2(u[h], u[h + 1]);
-                const float2 P = make_float2(pa[h], pa[h + 1]);
-                const float2 CF = make_float2(cf[h], cf[h + 1]);
-                const float2 L = make_float2(lap[h], lap[h + 1]);
-                float2 G = make_float2(1.0f, 1.0f);
-                if (SPONGE) G = __fmul2_rn(make_float2(gxy[h], gxy[h + 1]), make_float2(gz, gz));
+            for (int h = 0; h < 2; ++h) {
+                const float2 U = u.pair(h), Pp = pa.pair(h), CF = cf.pair(h),
+                             L = lap.pair(h);
+                float2 Gs = make_float2(1.0f, 1.0f);
+                if (SPONGE) Gs = __fmul2_rn(gxy.pair(h), make_float2(gz, gz));
                 float2 UN, WN = make_float2(0.0f, 0.0f);
                 if (DELTA) {
-                    const float2 w = __fmul2_rn(P, make_float2(isw_, isw_));
+                    const float2 w = __fmul2_rn(Pp, make_float2(isw_, isw_));
                     const float2 uu = __fmul2_rn(U, make_float2(isu_, isu_));
                     const float2 a = __ffma2_rn(CF, L, w);
-                    WN = SPONGE ? __fmul2_rn(G, a) : a;
-                    UN = SPONGE ? __ffma2_rn(G, uu, WN) : __fadd2_rn(uu, WN);
+                    WN = SPONGE ? __fmul2_rn(Gs, a) : a;
+                    UN = SPONGE ? __ffma2_rn(Gs, uu, WN) : __fadd2_rn(uu, WN);
                 } else {
                     // 2u - G u_prev rounded once: fma(-G, u_prev, u + u)
-                    const float2 nG = SPONGE ? make_float2(-G.x, -G.y)
+                    const float2 nG = SPONGE ? make_float2(-Gs.x, -Gs.y)
                                              : make_float2(-1.0f, -1.0f);
-                    const float2 tt = __ffma2_rn(nG, P, __fadd2_rn(U, U));
+                    const float2 tt = __ffma2_rn(nG, Pp, __fadd2_rn(U, U));
                     const float2 a = __ffma2_rn(CF, L, tt);
-                    UN = SPONGE ? __fmul2_rn(G, a) : a;
+                    UN = SPONGE ? __fmul2_rn(Gs, a) : a;
                 }
-                un[h] = UN.x; un[h + 1] = UN.y;
-                wn[h] = WN.x; wn[h + 1] = WN.y;
+                if (h) { un.b = UN; wn.b = WN; } else { un.a = UN; wn.a = WN; }
             }
         } else {
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                M G = SPONGE ? mul_rn(gxy[i], gz) : M(1);
+                M Gs = SPONGE ? mul_rn(gxy.get(i), gz) : M(1);
                 if (DELTA) {
-                    M w = mul_rn(pa[i], isw_);
-                    M uu = mul_rn(u[i], isu_);
-                    M a = fma_rn(cf[i], lap[i], w);
-                    wn[i] = SPONGE ? mul_rn(G, a) : a;
-                    un[i] = SPONGE ? fma_rn(G, uu, wn[i]) : add_rn(uu, wn[i]);
+                    M w = mul_rn(pa.get(i), isw_);
+                    M uu = mul_rn(u.get(i), isu_);
+                    M a = fma_rn(cf.get(i), lap.get(i), w);
+                    M wv = SPONGE ? mul_rn(Gs, a) : a;
+                    wn.set(i, wv);
+                    un.set(i, SPONGE ? fma_rn(Gs, uu, wv) : add_rn(uu, wv));
                 } else {
-                    M tt = fma_rn(-G, pa[i], add_rn(u[i], u[i]));
-                    M a = fma_rn(cf[i], lap[i], tt);
-                    un[i] = SPONGE ? mul_rn(G, a) : a;
-                    wn[i] = M(0);
+                    M tt = fma_rn(-Gs, pa.get(i), add_rn(u.get(i), u.get(i)));
+                    M a = fma_rn(cf.get(i), lap.get(i), tt);
+                    un.set(i, SPONGE ? mul_rn(Gs, a) : a);
+                    wn.set(i, M(0));
                 }
             }
         }
     }
 
     // sum of u'^2 over this thread's valid points (per-lane FP32 partials)
-    __device__ __forceinline__ void accumulate_norm(const M (&un)[4])
+    __device__ __forceinline__ void accumulate_norm(const G &un)
     {
-        if constexpr (std::is_same<M, float>::value && C::PACK) {
+        if constexpr (PK) {
             if (vx == 4) {
-                acc2 = __ffma2_rn(make_float2(un[0], un[1]), make_float2(un[0], un[1]), acc2);
-                acc2 = __ffma2_rn(make_float2(un[2], un[3]), make_float2(un[2], un[3]), acc2);
+                acc2 = __ffma2_rn(un.a, un.a, acc2);
+                acc2 = __ffma2_rn(un.b, un.b, acc2);
                 return;
             }
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            if (i < vx) acc = fma_rn(un[i], un[i], acc);
+            if (i < vx) acc = fma_rn(un.get(i), un.get(i), acc);
     }
 
     // ---- one u-plane iteration -----------------------------------------
-    // The register queue Q[0..8] holds this thread's points on planes
-    // z-4 .. z+4; the plane that just arrived lands in Q[8] and the queue
-    // shifts down one plane per iteration (a compact loop body keeps the
-    // hot loop inside the instruction cache).
+    // Queue entries 0..7 hold this thread's points on the 8 planes before the
+    // one that arrives now, which lands in entry 8 + P (P = phase within the
+    // trip); the compute plane is the one 4 back.  The trip loop shifts the
+    // queue by KP planes after its KP phases.
+    template <int P>
     __device__ __forceinline__ void iter(int t)
     {
         // (1) the plane of load t: append its centre values to the queue
@@ -628,7 +685,7 @@ struct Step {
             const T *pl = ubuf(slot);
 #pragma unroll
             for (int r = 0; r < PY; ++r)
-                S::ld4(pl + (PY * ty + r + R) * C::RW + HL + 4 * tx, Q[8][r]);
+                ld_grp<T, PK>(pl + (PY * ty + r + R) * C::RW + HL + 4 * tx, Q[8 + P][r]);
         }
         // (2) compute plane z = z0 + t - 8 once the queue is full
         if (t >= 2 * R) {
@@ -636,18 +693,18 @@ struct Step {
             const T *pl = ubuf((tg - R) % SU);
             unsigned ps = jg % SP;
             wait_or_abort(pfull(ps), (jg / SP) & 1u);
-            M yv[PY + 8][4];
+            G yv[PY + 8];
 #pragma unroll
             for (int j = 0; j < PY + 8; ++j)
-                S::ld4(pl + (PY * ty + j) * C::RW + HL + 4 * tx, yv[j]);
-            M lf[PY][4], rt[PY][4], pa[PY][4], cf[PY][4];
+                ld_grp<T, PK>(pl + (PY * ty + j) * C::RW + HL + 4 * tx, yv[j]);
+            G lf[PY], rt[PY], pa[PY], cf[PY];
 #pragma unroll
             for (int r = 0; r < PY; ++r) {
                 const T *row = pl + (PY * ty + r + R) * C::RW + HL + 4 * tx;
-                S::ld4(row - 4, lf[r]);
-                S::ld4(row + 4, rt[r]);
-                S::ld4(pbuf(ps, 0) + (PY * ty + r) * TX + 4 * tx, pa[r]);
-                St<typename C::CT>::ld4(
+                ld_grp<T, PK>(row - 4, lf[r]);
+                ld_grp<T, PK>(row + 4, rt[r]);
+                ld_grp<T, PK>(pbuf(ps, 0) + (PY * ty + r) * TX + 4 * tx, pa[r]);
+                ld_grp<typename C::CT, PK>(
                     reinterpret_cast<const typename C::CT *>(pbuf(ps, 1)) +
                         (PY * ty + r) * TX + 4 * tx, cf[r]);
             }
@@ -656,11 +713,10 @@ struct Step {
                 gz = gz_next;                       // loaded one plane ago
                 if (z + 1 < z1) gz_next = (M)__ldg(gz_ptr + z + 1);
             }
-
-            M lap[PY][4];
-#pragma unroll
-            for (int r = 0; r < PY; ++r) laplacian_row(yv, lf[r], rt[r], r, lap[r]);
             const int nl = nl_;
+            G lap[PY];
+#pragma unroll
+            for (int r = 0; r < PY; ++r) laplacian_row<P>(yv, lf[r], rt[r], r, lap[r]);
             // point sources: lap += wavelet[n] at the source cell (the loop
             // only finds the point; the add is a select over compile-time
             // indices, so lap stays in registers)
@@ -676,13 +732,13 @@ struct Step {
                             for (int r = 0; r < PY; ++r)
 #pragma unroll
                                 for (int i = 0; i < 4; ++i)
-                                    lap[r][i] = (k == r * 4 + i) ? add_rn(lap[r][i], wv) : lap[r][i];
+                                    lap[r].set(i, (k == r * 4 + i) ? add_rn(lap[r].get(i), wv) : lap[r].get(i));
                         }
                     }
                 }
             }
             // leapfrog update with the sponge
-            M un[PY][4], wn[PY][4];
+            G un[PY], wn[PY];
 #pragma unroll
             for (int r = 0; r < PY; ++r)
                 update_row(yv[r + R], pa[r], cf[r], lap[r], gxy[r], gz, un[r], wn[r]);
@@ -695,8 +751,8 @@ struct Step {
                 M so[4], sw[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    so[i] = DELTA ? mul_rn(un[r][i], su_) : un[r][i];
-                    sw[i] = DELTA ? mul_rn(wn[r][i], sw_) : M(0);
+                    so[i] = DELTA ? mul_rn(un[r].get(i), su_) : un[r].get(i);
+                    sw[i] = DELTA ? mul_rn(wn[r].get(i), sw_) : M(0);
                 }
                 accumulate_norm(un[r]);
                 if (vx == 4) {
@@ -726,21 +782,14 @@ struct Step {
                             for (int r = 0; r < PY; ++r)
 #pragma unroll
                                 for (int i = 0; i < 4; ++i)
-                                    v = (k == r * 4 + i) ? un[r][i] : v;
+                                    v = (k == r * 4 + i) ? un[r].get(i) : v;
                             sh->traces[(size_t)q.x * cap_ + n] = (float)v;
                         }
                     }
                 }
             }
         }
-        // (3) shift the queue by one plane
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-#pragma unroll
-            for (int r = 0; r < PY; ++r)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) Q[q][r][i] = Q[q + 1][r][i];
-        // (4) hand slots back: load tg - 4 (its last use, as the x/y plane,
+        // (3) hand slots back: load tg - 4 (its last use, as the x/y plane,
         // was this iteration) and the pointwise tile just used
         __syncwarp();
         if (lane == 0) {
@@ -749,6 +798,14 @@ struct Step {
         }
         if (t >= 2 * R) ++jg;
         ++tg;
+    }
+
+    __device__ __forceinline__ void shift_queue()
+    {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int r = 0; r < PY; ++r) Q[q][r] = Q[q + KP][r];
     }
 
     // One-sided puts of a freshly computed row segment into the halos of
@@ -825,8 +882,13 @@ struct Step {
         for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
             begin_item(it);
             const int T = z1 - z0 + 2 * R;
+            static_assert(KP == 2, "the trip loop below runs two phases");
 #pragma unroll 1
-            for (int t = 0; t < T; ++t) iter(t);
+            for (int tb = 0; tb < T; tb += KP) {
+                iter<0>(tb);
+                if (tb + 1 < T) iter<1>(tb + 1);
+                shift_queue();
+            }
             end_item(it);
         }
     }
