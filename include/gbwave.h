@@ -107,6 +107,10 @@ typedef struct {
                               model (load balance vs z-halo re-reads)     */
     double scale_u;        /* GW_F16S: power-of-two scale of u; 0: auto   */
     double scale_w;        /* GW_F16S: power-of-two scale of w; 0: auto   */
+    int persistent;        /* != 0: each chunk of steps is one launch whose
+                              CTAs wait for each other between steps (a
+                              bounded device-wide barrier; cooperative
+                              launch); needs GW_HALO_FUSED                */
 } gw_shot_desc;
 
 typedef struct {
@@ -123,8 +127,9 @@ typedef struct {
 } gw_domain_info;
 
 typedef struct {
-    int launches;          /* step-kernel launches timed                  */
-    double total_ms;       /* summed device time of those launches        */
+    int launches;          /* steps timed (a persistent launch counts each
+                              of its steps)                               */
+    double total_ms;       /* summed device time of the step kernels      */
     double halo_ms;        /* summed device time of separate halo kernels */
 } gw_kernel_stats;
 

@@ -86,6 +86,7 @@ struct gw_domain {
     char *d_maps = nullptr;
     unsigned *d_err = nullptr;
     int *d_step = nullptr;
+    unsigned *d_gbar = nullptr;           // barrier of persistent launches
     double *d_scratch = nullptr;          // 4 doubles for checks
     double *d_wavelet = nullptr;
     double *d_norms = nullptr;
@@ -122,6 +123,7 @@ struct gw_domain {
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_step, ev_halo;
+    std::vector<int> ev_steps;            // steps covered by each ev_step pair
     double acc_ms = 0, acc_halo_ms = 0;
     int acc_n = 0;
 
@@ -354,6 +356,8 @@ StepArgs step_args(gw_domain *d, int k)
     a.k = k;
     a.symmetric = d->symmetric ? 1 : 0;
     a.fused_halo = d->desc.halo_mode == GW_HALO_FUSED ? 1 : 0;
+    a.nk = 1;
+    a.gbar = d->d_gbar;
     return a;
 }
 
@@ -374,6 +378,27 @@ gw_status enqueue_chunk(gw_domain *d, int nk, cudaStream_t s, bool timed)
 {
     const bool sponge = d->desc.sponge > 0;
     const bool sep = d->desc.halo_mode == GW_HALO_SEPARATE && !d->halo.empty();
+    if (d->desc.persistent && !sep && nk > 1) {
+        // all nk steps in one launch, a device-wide barrier between steps
+        GW_TRY_CUDA(cudaMemsetAsync(d->d_gbar, 0, sizeof(unsigned), s));
+        StepArgs a = step_args(d, 0);
+        a.nk = nk;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (timed) {
+            e0 = pool_event(d);
+            e1 = pool_event(d);
+            GW_TRY_CUDA(cudaEventRecord(e0, s));
+        }
+        GW_TRY_CUDA(launch_step(d->dtype, d->cfg, sponge, d->grid, a, s));
+        if (timed) {
+            GW_TRY_CUDA(cudaEventRecord(e1, s));
+            d->ev_step.push_back({e0, e1});
+            d->ev_steps.push_back(nk);
+        }
+        GW_TRY_CUDA(launch_chunk_end(d->d_shot, 1, d->d_partials, d->nitems, nk,
+                                     d->d_err, s));
+        return GW_OK;
+    }
     for (int k = 0; k < nk; ++k) {
         StepArgs a = step_args(d, k);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -386,6 +411,7 @@ gw_status enqueue_chunk(gw_domain *d, int nk, cudaStream_t s, bool timed)
         if (timed) {
             GW_TRY_CUDA(cudaEventRecord(e1, s));
             d->ev_step.push_back({e0, e1});
+            d->ev_steps.push_back(1);
         }
         if (sep) {
             cudaEvent_t h0 = nullptr, h1 = nullptr;
@@ -429,11 +455,12 @@ gw_status ensure_graph(gw_domain *d)
 
 void harvest_events(gw_domain *d)
 {
-    for (auto &p : d->ev_step) {
+    for (size_t i = 0; i < d->ev_step.size(); ++i) {
+        auto &p = d->ev_step[i];
         float ms = 0;
         if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) {
             d->acc_ms += ms;
-            ++d->acc_n;
+            d->acc_n += i < d->ev_steps.size() ? d->ev_steps[i] : 1;
         }
         d->ev_pool.push_back(p.first);
         d->ev_pool.push_back(p.second);
@@ -446,6 +473,7 @@ void harvest_events(gw_domain *d)
         d->ev_pool.push_back(p.second);
     }
     d->ev_step.clear();
+    d->ev_steps.clear();
     d->ev_halo.clear();
 }
 
@@ -641,6 +669,7 @@ gw_status gw_domain_create(gw_ctx *c, const gw_shot_desc *desc, int px, int py,
     d->d_maps = m + off_maps;
     d->d_err = reinterpret_cast<unsigned *>(m + off_err);
     d->d_step = reinterpret_cast<int *>(m + off_step);
+    d->d_gbar = reinterpret_cast<unsigned *>(m + off_err + 32);
     d->d_scratch = reinterpret_cast<double *>(m + off_scr);
     d->d_wavelet = reinterpret_cast<double *>(m + off_wl);
     d->d_norms = reinterpret_cast<double *>(m + off_norm);

@@ -88,7 +88,9 @@ struct StepArgs {
     char *seg_base;        // segment base (symmetric address translation)
     long long rank_stride; // bytes between rank segments
     int nitems;
-    int k;                 // step index within the current chunk
+    int k;                 // step index within the chunk of the first step
+    int nk;                // steps this launch performs (persistent: > 1)
+    unsigned *gbar;        // device-wide barrier counter (zero at launch)
     int symmetric;         // 1: neighbour address = own + (dr * stride)
     int fused_halo;        // 1: epilogue stores into neighbours' halos
 };

@@ -109,4 +109,39 @@ __device__ __forceinline__ void prefetch_tensormap(const void *map)
                  :: "l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// ---- device-wide barrier between the steps of a persistent launch ------
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_gpu_add(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Order this thread's generic-proxy global writes before later async-proxy
+// (TMA) reads of the same memory.
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Wait until *count >= target; false after kWaitLimitNs or once *abortf is
+// set (the caller then latches an error and leaves).
+__device__ __forceinline__ bool wait_count(const unsigned *count, unsigned target,
+                                           volatile int *abortf)
+{
+    unsigned long long t0 = global_timer();
+    for (uint32_t i = 0;; ++i) {
+        if (ld_acquire_gpu(count) >= target) return true;
+        if (*abortf) return false;
+        __nanosleep(64);
+        if ((i & 63u) == 63u && global_timer() - t0 > kWaitLimitNs) return false;
+    }
+}
+
 }  // namespace gw

@@ -306,6 +306,7 @@ struct Step {
 
     // consumer
     unsigned tg, jg;           // u loads / pointwise planes consumed
+    int kk;                    // step index within the chunk being computed
     bool aborted;              // a wait of this thread gave up
 
     // current item (cached in registers: the stores below may alias the
@@ -379,10 +380,21 @@ struct Step {
         const uint64_t pol_first = policy_evict_first();
         const uint64_t pol_last = policy_evict_last();
         unsigned L = 0, P = 0;
+        for (int k = 0; k < A.nk; ++k) {
+        if (k > 0) {
+            // the previous step's stores must be complete everywhere before
+            // this CTA streams the planes of the next one
+            if (!wait_count(A.gbar, (unsigned)k * gridDim.x, abortf())) {
+                if (!*abortf()) atomicOr(A.err, ERRB_TIMEOUT);
+                *abortf() = 1;
+                goto drain;
+            }
+            fence_proxy_async_global();
+        }
         for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
             const Item I = A.items[it];
             const SubDev &s = A.subs[I.sub];
-            const int p = (*A.shots[s.shot].step + A.k) & 1;
+            const int p = (*A.shots[s.shot].step + A.k + k) & 1;
             const char *base = static_cast<const char *>(A.maps) +
                                (size_t)I.sub * kMapsPerSub * 128;
             const char *map_u = base + (p ? MAP_U1_HALO : MAP_U0_HALO) * 128;
@@ -418,6 +430,7 @@ struct Step {
                 }
             }
         }
+        }
     drain:
         // leave only after every copy issued into this CTA's shared memory
         // has landed (bounded)
@@ -449,7 +462,7 @@ struct Step {
         cap_ = sh->cap;
         gz_ptr = sh->gz + sd->gz0;
         if (SPONGE) gz_next = (M)__ldg(gz_ptr + z0);
-        n = *sh->step + A.k;
+        n = *sh->step + kk;
         par = n & 1;
         unext = reinterpret_cast<T *>(sd->u[par ^ 1]);
         wbuf = reinterpret_cast<T *>(sd->w);
@@ -539,7 +552,7 @@ struct Step {
         if (tid == 0) {
             double s = 0.0;
             for (int w = 0; w < C::NCW; ++w) s += red()[w];
-            A.partials[(size_t)A.k * A.nitems + it] = s;
+            A.partials[(size_t)kk * A.nitems + it] = s;
         }
     }
 
@@ -879,17 +892,28 @@ struct Step {
         ty = tid / C::NTX;
         aborted = false;
         tg = jg = 0;
-        for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
-            begin_item(it);
-            const int T = z1 - z0 + 2 * R;
-            static_assert(KP == 2, "the trip loop below runs two phases");
+        for (int k = 0; k < A.nk; ++k) {
+            kk = A.k + k;
+            for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
+                begin_item(it);
+                const int T = z1 - z0 + 2 * R;
+                static_assert(KP == 2, "the trip loop below runs two phases");
 #pragma unroll 1
-            for (int tb = 0; tb < T; tb += KP) {
-                iter<0>(tb);
-                if (tb + 1 < T) iter<1>(tb + 1);
-                shift_queue();
+                for (int tb = 0; tb < T; tb += KP) {
+                    iter<0>(tb);
+                    if (tb + 1 < T) iter<1>(tb + 1);
+                    shift_queue();
+                }
+                end_item(it);
             }
-            end_item(it);
+            if (k + 1 < A.nk) {
+                // arrive at the device-wide barrier once this CTA's stores of
+                // the step (interior and halo puts) are visible
+                __threadfence();
+                fence_proxy_async_global();
+                consumer_sync(C::NT);
+                if (tid == 0) red_release_gpu_add(A.gbar, 1u);
+            }
         }
     }
 };
@@ -921,8 +945,23 @@ static cudaError_t launch_cfg(bool sponge, int grid, const StepArgs &a,
         if (e != cudaSuccess) return e;
         attr_done[sponge] = true;
     }
-    kern<<<grid, C::THREADS, C::SMEM, s>>>(a);
-    return cudaGetLastError();
+    if (a.nk <= 1) {
+        kern<<<grid, C::THREADS, C::SMEM, s>>>(a);
+        return cudaGetLastError();
+    }
+    // several steps in one launch: the CTAs wait for each other between
+    // steps, so they must all be resident (cooperative launch)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(C::THREADS);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 template <class C, bool DELTA>

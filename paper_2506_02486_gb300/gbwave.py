@@ -52,6 +52,7 @@ class gw_shot_desc(ctypes.Structure):
         ("halo_mode", ctypes.c_int), ("chunk", ctypes.c_int),
         ("tile", ctypes.c_int), ("zchunk", ctypes.c_int),
         ("scale_u", ctypes.c_double), ("scale_w", ctypes.c_double),
+        ("persistent", ctypes.c_int),
     ]
 
 
@@ -275,7 +276,7 @@ def gw_fence(ctx: int, stream=None):
 def shot_desc(nx, ny, nz, *, h=10.0, courant=0.0, dt=0.0, nsteps=0,
               dtype="f32", sponge=0, sponge_a=0.0, periodic=0,
               halo_mode=GW_HALO_FUSED, chunk=0, tile=0, zchunk=0,
-              scale_u=0.0, scale_w=0.0) -> gw_shot_desc:
+              scale_u=0.0, scale_w=0.0, persistent=0) -> gw_shot_desc:
     d = gw_shot_desc()
     d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
     d.h, d.courant, d.dt = float(h), float(courant), float(dt)
@@ -285,6 +286,7 @@ def shot_desc(nx, ny, nz, *, h=10.0, courant=0.0, dt=0.0, nsteps=0,
     d.periodic, d.halo_mode = int(periodic), int(halo_mode)
     d.chunk, d.tile, d.zchunk = int(chunk), int(tile), int(zchunk)
     d.scale_u, d.scale_w = float(scale_u), float(scale_w)
+    d.persistent = int(persistent)
     return d
 
 

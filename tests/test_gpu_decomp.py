@@ -26,6 +26,17 @@ def reference():
     return vel, src, rec, base
 
 
+def test_persistent_chunks_are_bitwise(reference):
+    """K steps in one launch (device-wide barrier between steps) give the
+    bits of one launch per step, undecomposed and 2 x 2 x 2."""
+    vel, src, rec, base = reference
+    for dec in ((1, 1, 1), (2, 2, 2)):
+        g = gpu_run(vel, 60, src=src, f_peak=40.0, receivers=rec, sponge=10,
+                    px=dec[0], py=dec[1], pz=dec[2], persistent=1, chunk=7)
+        assert np.array_equal(g["u32"], base["u32"])
+        assert np.array_equal(g["traces"], base["traces"])
+
+
 @pytest.mark.parametrize("px,py,pz,symmetric,mode,split", [
     (2, 2, 2, True, gw.GW_HALO_FUSED, (None, None, None)),
     (2, 2, 2, True, gw.GW_HALO_SEPARATE, (None, None, None)),
