@@ -315,6 +315,40 @@ gw_status gw_check_fields_noalloc(const void *u_cur, const void *u_prev,
                                   int nz, int px, double scale_u,
                                   double *out_dev, gw_stream stream);
 
+/* ------------------------------------------------------------------ */
+/* batches: several independent shots advanced by the same launches    */
+
+/* Group nshots existing domains of one context (one storage type; fused or
+ * no halos) so that every launch covers the work items of all of them:
+ * shots with the same kernel tile share one launch per step (or per chunk
+ * in persistent mode); shots with different tiles form separate groups
+ * launched one after the other.  Each shot keeps its own model, sources,
+ * receivers, step counter and logs, read through its domain.  chunk: steps
+ * per CUDA-graph chunk (0: 25; < 0: plain launches).  persistent != 0: one
+ * cooperative launch per chunk with a device-wide barrier between steps.
+ * The batch allocates its tables from the segment; destroy it before its
+ * domains. */
+gw_status gw_batch_create(gw_ctx *ctx, int nshots, gw_domain *const *shots,
+                          int chunk, int persistent, gw_batch **out);
+gw_status gw_batch_destroy(gw_batch *b);
+/* Advance every shot of the batch by nsteps steps on `stream`. */
+gw_status gw_batch_step(gw_batch *b, int nsteps, gw_stream stream);
+/* Launch groups, total CTAs and work items of one step of the batch. */
+gw_status gw_batch_info(gw_batch *b, int *groups, int *ctas, int *items);
+/* Per-step device time of the batch's step kernels while enabled
+ * (plain launches; stats as for gw_kernel_stats_get). */
+gw_status gw_batch_timing(gw_batch *b, int enable);
+gw_status gw_batch_stats_get(gw_batch *b, gw_kernel_stats *out);
+
+/* Autotuner: time every kernel tile available for this storage type on a
+ * scratch domain shaped like `desc` with a px x py x pz split (homogeneous
+ * model, `steps` timed steps after a warm-up), using free segment memory,
+ * and return the fastest tile (for gw_shot_desc.tile) and its time per
+ * step.  Results are cached per (shape, split, storage, halo mode) for the
+ * life of the context.  Synchronises. */
+gw_status gw_autotune(gw_ctx *ctx, const gw_shot_desc *desc, int px, int py,
+                      int pz, int steps, int *best_tile, double *best_ms);
+
 /* Record the device time of every step-kernel launch (CUDA events) while
  * enabled; gw_kernel_stats_get returns the totals and resets them. */
 gw_status gw_kernel_timing(gw_domain *d, int enable);

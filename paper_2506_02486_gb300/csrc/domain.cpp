@@ -9,13 +9,12 @@
 #include <cmath>
 #include <cstring>
 
-#include "gw_internal.h"
+#include "domain_impl.h"
 
 using namespace gw;
 
 namespace {
 
-constexpr int kDefaultChunk = 25;
 constexpr size_t kStageBytes = size_t(256) << 20;   // host<->device slabs
 
 // FP64 host precompute of the scheme's constants (the library's own; the
@@ -68,68 +67,6 @@ CUtensorMapDataType tma_type(int elem_size, bool bf16)
 
 }  // namespace
 
-struct gw_domain {
-    gw_ctx *ctx = nullptr;
-    gw_shot_desc desc{};
-    int dtype = DT_F32;
-    bool delta = false;
-    int np[3] = {1, 1, 1};
-    bool symmetric = true;
-    std::vector<int> split[3];
-    std::vector<SubDev> subs;
-    std::vector<gw_gptr> allocs;          // every allocation we own
-    gw_gptr g_fields[4] = {0, 0, 0, 0};   // u0, u1, w, coef
-    size_t device_bytes = 0;
-    // device metadata
-    SubDev *d_subs = nullptr;
-    ShotDev *d_shot = nullptr;
-    char *d_maps = nullptr;
-    unsigned *d_err = nullptr;
-    int *d_step = nullptr;
-    unsigned *d_gbar = nullptr;           // barrier of persistent launches
-    double *d_scratch = nullptr;          // 4 doubles for checks
-    double *d_wavelet = nullptr;
-    double *d_norms = nullptr;
-    double *d_gtab = nullptr;             // gx | gy | gz
-    int4 *d_src = nullptr;
-    int4 *d_rec = nullptr;
-    float *d_traces = nullptr;
-    Item *d_items = nullptr;
-    double *d_partials = nullptr;
-    HaloDesc *d_halo = nullptr;
-    gw_gptr g_rec = 0, g_traces = 0, g_items = 0;
-    ShotDev shot{};
-    // schedule
-    int cfg = 0;
-    TileInfo ti{};
-    int grid = 0, nitems = 0, chunk = kDefaultChunk, zc = 0;
-    std::vector<Item> items;
-    std::vector<HaloDesc> halo;
-    long long halo_total = 0;
-    // sources and receivers (host copies)
-    std::vector<int4> srcs;
-    std::vector<std::vector<double>> wavelets;
-    int nrec = 0;
-    // model
-    double dt = 0, vmax = 0, courant = 0;
-    bool model_set = false;
-    double su = 1, sw = 1;
-    int step = 0;                         // steps enqueued
-    cudaStream_t last = nullptr;
-    // graphs
-    cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    // timing
-    bool timing = false;
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_step, ev_halo;
-    std::vector<int> ev_steps;            // steps covered by each ev_step pair
-    double acc_ms = 0, acc_halo_ms = 0;
-    int acc_n = 0;
-
-    int nsub() const { return (int)subs.size(); }
-    int esize() const { return dtype_size(dtype); }
-};
 
 namespace {
 
@@ -194,63 +131,9 @@ gw_status encode_map(gw_domain *d, CUtensorMap *out, char *base, const SubDev &s
     return GW_OK;
 }
 
-// Work items in z-chunk-major order; the chunk size balances rounds of
-// `grid` CTAs against the 8 extra planes every item streams.
 void build_items(gw_domain *d)
 {
-    const int TX = d->ti.tx, TY = d->ti.ty;
-    long long ncols = 0;
-    int nzmax = 0;
-    for (const SubDev &s : d->subs) {
-        ncols += (long long)((s.nx + TX - 1) / TX) * ((s.ny + TY - 1) / TY);
-        nzmax = std::max(nzmax, s.nz);
-    }
-    int zc = d->desc.zchunk;
-    if (zc <= 0) {
-        // Items of at most 128 planes (measured on 512^3: one item per CTA
-        // and 32-plane items both run slower), chosen to fill the last
-        // round of `grid` CTAs: cost = rounds * (planes + 8 * alpha), where
-        // a streamed-only halo plane costs alpha = 0.5 of a computed one.
-        double best = 1e300;
-        int best_n = 1;
-        const int lo = std::max(1, (nzmax + 127) / 128);
-        const int hi = std::max(lo, nzmax / 32);
-        for (int nzc = lo; nzc <= hi; ++nzc) {
-            long long items = ncols * nzc;
-            long long rounds = (items + d->grid - 1) / d->grid;
-            double cost = (double)rounds * ((double)nzmax / nzc + 8 * 0.5);
-            if (cost < best - 1e-9) {
-                best = cost;
-                best_n = nzc;
-            }
-        }
-        zc = (nzmax + best_n - 1) / best_n;
-    }
-    d->zc = zc;
-    struct Key { int z, sub, y, x; };
-    std::vector<std::pair<Key, Item>> v;
-    for (int si = 0; si < d->nsub(); ++si) {
-        const SubDev &s = d->subs[si];
-        int nzc = (s.nz + zc - 1) / zc;
-        for (int c = 0; c < nzc; ++c) {
-            int z0 = (int)((long long)s.nz * c / nzc);
-            int z1 = (int)((long long)s.nz * (c + 1) / nzc);
-            if (z1 <= z0) continue;
-            for (int y0 = 0; y0 < s.ny; y0 += TY)
-                for (int x0 = 0; x0 < s.nx; x0 += TX) {
-                    Item it{si, x0 | (y0 << 16), z0, z1};
-                    v.push_back({Key{s.gz0 + z0, si, y0, x0}, it});
-                }
-        }
-    }
-    std::stable_sort(v.begin(), v.end(), [](const auto &a, const auto &b) {
-        if (a.first.z != b.first.z) return a.first.z < b.first.z;
-        if (a.first.sub != b.first.sub) return a.first.sub < b.first.sub;
-        if (a.first.y != b.first.y) return a.first.y < b.first.y;
-        return a.first.x < b.first.x;
-    });
-    d->items.clear();
-    for (auto &p : v) d->items.push_back(p.second);
+    d->zc = make_items(d->subs, d->ti, d->grid, d->desc.zchunk, d->items);
     d->nitems = (int)d->items.size();
 }
 
@@ -509,6 +392,70 @@ gw_status check_dom(gw_domain *d)
 }
 
 }  // namespace
+
+namespace gw {
+
+// Work items in z-chunk-major order (CTAs running together hold
+// neighbouring columns at the same depth).
+int make_items(const std::vector<SubDev> &subs, const TileInfo &ti, int grid,
+               int zchunk, std::vector<Item> &items, int sub_base)
+{
+    const int TX = ti.tx, TY = ti.ty;
+    long long ncols = 0;
+    int nzmax = 0;
+    for (const SubDev &s : subs) {
+        ncols += (long long)((s.nx + TX - 1) / TX) * ((s.ny + TY - 1) / TY);
+        nzmax = std::max(nzmax, s.nz);
+    }
+    int zc = zchunk;
+    if (zc <= 0) {
+        // Items of at most 128 planes (measured on 512^3: one item per CTA
+        // and 32-plane items both run slower), chosen to fill the last
+        // round of `grid` CTAs: cost = rounds * (planes + 8 * alpha), where
+        // a streamed-only halo plane costs alpha = 0.5 of a computed one.
+        double best = 1e300;
+        int best_n = 1;
+        const int lo = std::max(1, (nzmax + 127) / 128);
+        const int hi = std::max(lo, nzmax / 32);
+        for (int nzc = lo; nzc <= hi; ++nzc) {
+            long long n = ncols * nzc;
+            long long rounds = (n + grid - 1) / grid;
+            double cost = (double)rounds * ((double)nzmax / nzc + 8 * 0.5);
+            if (cost < best - 1e-9) {
+                best = cost;
+                best_n = nzc;
+            }
+        }
+        zc = (nzmax + best_n - 1) / best_n;
+    }
+    struct Key { int z, sub, y, x; };
+    std::vector<std::pair<Key, Item>> v;
+    for (int si = 0; si < (int)subs.size(); ++si) {
+        const SubDev &s = subs[si];
+        int nzc = (s.nz + zc - 1) / zc;
+        for (int c = 0; c < nzc; ++c) {
+            int z0 = (int)((long long)s.nz * c / nzc);
+            int z1 = (int)((long long)s.nz * (c + 1) / nzc);
+            if (z1 <= z0) continue;
+            for (int y0 = 0; y0 < s.ny; y0 += TY)
+                for (int x0 = 0; x0 < s.nx; x0 += TX) {
+                    Item it{sub_base + si, x0 | (y0 << 16), z0, z1};
+                    v.push_back({Key{s.gz0 + z0, si, y0, x0}, it});
+                }
+        }
+    }
+    std::stable_sort(v.begin(), v.end(), [](const auto &a, const auto &b) {
+        if (a.first.z != b.first.z) return a.first.z < b.first.z;
+        if (a.first.sub != b.first.sub) return a.first.sub < b.first.sub;
+        if (a.first.y != b.first.y) return a.first.y < b.first.y;
+        return a.first.x < b.first.x;
+    });
+    items.clear();
+    for (auto &p : v) items.push_back(p.second);
+    return zc;
+}
+
+}  // namespace gw
 
 // ================================================================ C ABI
 

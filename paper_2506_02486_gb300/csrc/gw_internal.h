@@ -87,6 +87,8 @@ struct gw_ctx {
     std::vector<cudaStream_t> put_streams;
     std::recursive_mutex mu;
     int num_sms = 0;
+    // autotuner results: shape/split/type key -> (tile, ms per step)
+    std::map<std::string, std::pair<int, double>> tuned;
 
     char *rank_base(int r) const { return base + (size_t)r * rank_bytes; }
 };

@@ -117,6 +117,15 @@ _SIGS = {
     "gw_check_fields_noalloc": [_P, _P, _P, _I, _I, _I, _I, _I, _D, _P, _P],
     "gw_kernel_timing": [_P, _I],
     "gw_kernel_stats_get": [_P, ctypes.POINTER(gw_kernel_stats)],
+    "gw_batch_create": [_P, _I, _P, _I, _I, ctypes.POINTER(_P)],
+    "gw_batch_destroy": [_P],
+    "gw_batch_step": [_P, _I, _P],
+    "gw_batch_info": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                      ctypes.POINTER(_I)],
+    "gw_batch_timing": [_P, _I],
+    "gw_batch_stats_get": [_P, ctypes.POINTER(gw_kernel_stats)],
+    "gw_autotune": [_P, ctypes.POINTER(gw_shot_desc), _I, _I, _I, _I,
+                    ctypes.POINTER(_I), ctypes.POINTER(_D)],
     "gw_state_bytes": [_P, ctypes.POINTER(_SZ)],
     "gw_save_state": [_P, _P],
     "gw_load_state": [_P, _P],
@@ -424,6 +433,52 @@ def gw_kernel_stats_get(dom: int) -> dict:
            "gw_kernel_stats_get")
     return {"launches": s.launches, "total_ms": s.total_ms,
             "halo_ms": s.halo_ms}
+
+
+def gw_batch_create(ctx: int, doms, chunk: int = 0,
+                    persistent: bool = False) -> int:
+    arr = (_P * len(doms))(*doms)
+    h = _P()
+    _check(lib().gw_batch_create(ctx, len(doms), ctypes.cast(arr, _P),
+                                 int(chunk), int(bool(persistent)),
+                                 ctypes.byref(h)), "gw_batch_create")
+    return h.value
+
+
+def gw_batch_destroy(b: int):
+    _check(lib().gw_batch_destroy(b), "gw_batch_destroy")
+
+
+def gw_batch_step(b: int, nsteps: int, stream=None):
+    _check(lib().gw_batch_step(b, int(nsteps), _stream(stream)),
+           "gw_batch_step")
+
+
+def gw_batch_info(b: int) -> dict:
+    g, c, i = _I(), _I(), _I()
+    _check(lib().gw_batch_info(b, ctypes.byref(g), ctypes.byref(c),
+                               ctypes.byref(i)), "gw_batch_info")
+    return {"groups": g.value, "ctas": c.value, "items": i.value}
+
+
+def gw_batch_timing(b: int, enable: bool):
+    _check(lib().gw_batch_timing(b, int(bool(enable))), "gw_batch_timing")
+
+
+def gw_batch_stats_get(b: int) -> dict:
+    s = gw_kernel_stats()
+    _check(lib().gw_batch_stats_get(b, ctypes.byref(s)), "gw_batch_stats_get")
+    return {"launches": s.launches, "total_ms": s.total_ms,
+            "halo_ms": s.halo_ms}
+
+
+def gw_autotune(ctx: int, desc: gw_shot_desc, px: int = 1, py: int = 1,
+                pz: int = 1, steps: int = 10) -> tuple[int, float]:
+    t, ms = _I(), _D()
+    _check(lib().gw_autotune(ctx, ctypes.byref(desc), int(px), int(py),
+                             int(pz), int(steps), ctypes.byref(t),
+                             ctypes.byref(ms)), "gw_autotune")
+    return t.value, ms.value
 
 
 def gw_state_bytes(dom: int) -> int:

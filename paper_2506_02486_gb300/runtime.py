@@ -126,3 +126,38 @@ class Shot:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Several shots of one segment advanced by shared launches."""
+
+    def __init__(self, seg: Segment, shots, chunk: int = 0,
+                 persistent: bool = False):
+        self.seg = seg
+        self.shots = list(shots)
+        self.h = gw.gw_batch_create(seg.ctx, [s.dom for s in self.shots],
+                                    chunk, persistent)
+
+    @property
+    def info(self) -> dict:
+        return gw.gw_batch_info(self.h)
+
+    def step(self, n: int, stream=None):
+        gw.gw_batch_step(self.h, n, stream)
+
+    def timing(self, enable: bool):
+        gw.gw_batch_timing(self.h, enable)
+
+    def stats(self) -> dict:
+        return gw.gw_batch_stats_get(self.h)
+
+    def close(self):
+        if self.h:
+            gw.gw_batch_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,162 @@
+"""Batched multi-shot launches: shots of different sizes, tiles, sponge
+settings and decompositions advanced together by gw_batch_step.
+
+Each shot of a batch must end bit-identical (wavefield and receiver traces)
+to the same shot stepped alone with the same kernel tile: the per-point
+arithmetic does not depend on which launch, CTA or z-chunk computes a
+point.  Per-step norms are FP64 sums over a different set of work items,
+so they agree to rounding (1e-12 relative).
+"""
+
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import ensure_built
+from paper_2506_02486_gb300 import gbwave as gw
+from paper_2506_02486_gb300.runtime import Batch, Segment, Shot, shot_bytes
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 60
+# (nx, ny, nz, px, py, pz, sponge, tile)
+SHOTS = [
+    (48, 48, 48, 1, 1, 1, 8, 0),
+    (64, 40, 56, 1, 1, 1, 8, 0),
+    (37, 41, 29, 1, 1, 1, 0, 0),
+    (64, 48, 40, 2, 1, 1, 8, 0),
+    (40, 40, 72, 1, 1, 2, 8, 2),
+]
+
+
+def _make(seg, k, spec, dtype):
+    nx, ny, nz, px, py, pz, sponge, tile = spec
+    s = Shot(seg, nx, ny, nz, px=px, py=py, pz=pz, nsteps=STEPS,
+             dtype=dtype, sponge=sponge, tile=tile)
+    s.set_model(workloads.layered(nx, ny, nz, seed=100 + k))
+    s.add_ricker((nx // 2, ny // 3, nz // 2), 30.0)
+    s.set_receivers(workloads.lattice_receivers(nx, ny, nz // 4, n=3,
+                                                margin=2))
+    return s
+
+
+def _result(s):
+    return {"u": s.u(f64=False), "traces": s.traces(STEPS),
+            "norms": s.norms(STEPS)}
+
+
+def _seg_bytes(dtype):
+    return sum(shot_bytes(nx, ny, nz, dtype, STEPS, 9, px, py, pz)
+               for nx, ny, nz, px, py, pz, _, _ in SHOTS)
+
+
+@pytest.mark.parametrize("dtype,mode", [
+    ("f32", "graphs"), ("f32", "plain"), ("f32", "persistent"),
+    ("bf16", "graphs"), ("f16s", "persistent"), ("f64", "graphs")])
+def test_batched_shots_match_alone(dtype, mode):
+    ensure_built()
+    alone = []
+    with Segment(2 * _seg_bytes(dtype), nranks=2) as seg:
+        for k, spec in enumerate(SHOTS):
+            with _make(seg, k, spec, dtype) as s:
+                s.step(STEPS)
+                s.sync()
+                alone.append(_result(s))
+    chunk = -25 if mode == "plain" else 0
+    with Segment(2 * _seg_bytes(dtype), nranks=2) as seg:
+        shots = [_make(seg, k, spec, dtype) for k, spec in enumerate(SHOTS)]
+        try:
+            with Batch(seg, shots, chunk=chunk,
+                       persistent=(mode == "persistent")) as b:
+                info = b.info
+                # tile 2 and the sponge-free shot form their own groups
+                assert info["groups"] == 3
+                b.step(STEPS - 20)
+                b.step(20)
+                shots[0].sync()
+            for k, s in enumerate(shots):
+                r = _result(s)
+                a = alone[k]
+                assert np.array_equal(r["u"], a["u"]), k
+                assert np.array_equal(r["traces"], a["traces"]), k
+                np.testing.assert_allclose(r["norms"], a["norms"],
+                                           rtol=1e-12, atol=0)
+                assert np.abs(a["u"]).max() > 0
+        finally:
+            for s in shots:
+                s.close()
+
+
+def test_batch_then_alone_continues_the_same_shot():
+    """A shot stepped partly in a batch and partly alone equals a shot
+    stepped alone throughout (the batch advances the shot's own step)."""
+    ensure_built()
+    spec = SHOTS[0]
+    with Segment(_seg_bytes("f32")) as seg:
+        with _make(seg, 0, spec, "f32") as s:
+            s.step(STEPS)
+            s.sync()
+            ref = _result(s)
+        with _make(seg, 0, spec, "f32") as s, _make(seg, 1, SHOTS[1],
+                                                    "f32") as t:
+            with Batch(seg, [s, t]) as b:
+                b.step(30)
+            s.step(STEPS - 30)
+            s.sync()
+            r = _result(s)
+    assert np.array_equal(r["u"], ref["u"])
+    assert np.array_equal(r["traces"], ref["traces"])
+
+
+def test_batch_rejects_mixed_types_and_separate_halos():
+    ensure_built()
+    with Segment(_seg_bytes("f32") * 4, nranks=2) as seg:
+        a = _make(seg, 0, SHOTS[0], "f32")
+        b = _make(seg, 1, SHOTS[0], "bf16")
+        nx, ny, nz = 48, 48, 48
+        c = Shot(seg, nx, ny, nz, px=2, nsteps=STEPS, halo_mode=1)
+        c.set_model(workloads.homogeneous(nx, ny, nz))
+        try:
+            with pytest.raises(gw.GWError) as e:
+                Batch(seg, [a, b])
+            assert e.value.status == gw.GW_ERR_ARG
+            with pytest.raises(gw.GWError) as e:
+                Batch(seg, [a, c])
+            assert e.value.status == gw.GW_ERR_ARG
+        finally:
+            for s in (a, b, c):
+                s.close()
+
+
+def test_batch_timing_counts_steps():
+    ensure_built()
+    with Segment(_seg_bytes("f32")) as seg:
+        shots = [_make(seg, k, spec, "f32")
+                 for k, spec in enumerate(SHOTS[:2])]
+        try:
+            with Batch(seg, shots) as b:
+                b.timing(True)
+                b.step(10)
+                st = b.stats()
+            assert st["launches"] == 10
+            assert st["total_ms"] > 0
+        finally:
+            for s in shots:
+                s.close()
+
+
+def test_autotune_picks_an_available_tile_and_caches_it():
+    ensure_built()
+    n = 96
+    with Segment(6 * shot_bytes(n, n, n, "f32", 16)) as seg:
+        d = gw.shot_desc(n, n, n, nsteps=16, sponge=10)
+        t1, ms1 = gw.gw_autotune(seg.ctx, d, 1, 1, 1, 5)
+        t2, ms2 = gw.gw_autotune(seg.ctx, d, 1, 1, 1, 5)
+        assert t1 >= 1 and ms1 > 0
+        assert (t1, ms1) == (t2, ms2)
+        # the chosen tile builds and runs
+        with Shot(seg, n, n, n, nsteps=16, sponge=10, tile=t1) as s:
+            s.set_model(workloads.homogeneous(n, n, n))
+            s.step(4)
+            s.sync()
+            assert s.info["tile"] == t1
