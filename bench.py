@@ -330,6 +330,86 @@ def run_e2e(seg, shot, steps):
     return el, h2d, d2h
 
 
+BATCH_SEED = 2508
+BATCH_STEPS = 300
+BATCH_CHUNK = 25
+
+
+def run_batch(dtype="f32", *, seed=BATCH_SEED, steps=BATCH_STEPS,
+              chunk=BATCH_CHUNK, autotune=True, persistent=True,
+              sequential=False, warmup=BATCH_CHUNK):
+    """64 independent cubic shots (sides drawn from {96..256} step 16, each
+    with its own layered model and source, 20-cell sponge, 20 Hz) advanced
+    together: one launch per tile group per K-step chunk, chunks replayed
+    from CUDA graphs, tiles per grid side from the autotuner.  Returns a
+    dict of aggregate Gpts/s and the schedule."""
+    import torch
+    import workloads
+    from paper_2506_02486_gb300 import gbwave as gw
+    from paper_2506_02486_gb300.runtime import Batch, Segment, Shot, shot_bytes
+    plan = workloads.batch_shots(seed, n=64, nsteps=steps)
+    total = sum(shot_bytes(b.side, b.side, b.side, dtype, steps + warmup, 16)
+                for b in plan)
+    pts = sum(b.side ** 3 for b in plan)
+    out = {"shots": len(plan), "points": pts, "steps": steps, "chunk": chunk,
+           "seed": seed, "dtype": dtype, "persistent": persistent}
+    with Segment(total + (2 << 30)) as seg:
+        tiles = {}
+        t0 = time.perf_counter()
+        if autotune:
+            descs = [gw.shot_desc(b.side, b.side, b.side, nsteps=steps,
+                                  dtype=dtype, sponge=b.sponge) for b in plan]
+            for b, t in zip(plan, gw.gw_plan_tiles(seg.ctx, descs, 20)):
+                tiles[b.side] = t
+        out["autotune_s"] = time.perf_counter() - t0
+        out["tiles"] = {str(k): v for k, v in tiles.items()}
+        shots = []
+        try:
+            for b in plan:
+                s = Shot(seg, b.side, b.side, b.side, nsteps=steps + warmup,
+                         dtype=dtype, sponge=b.sponge,
+                         tile=tiles.get(b.side, 0))
+                shots.append(s)
+                s.set_model(b.model())
+                s.add_ricker(b.source, 20.0)
+                s.set_receivers(workloads.lattice_receivers(
+                    b.side, b.side, b.sponge, n=4, margin=b.sponge))
+            st = torch.cuda.current_stream()
+            if sequential:
+                # the same shots one after the other, each its own launches
+                for s in shots:
+                    s.step(warmup, st)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for s in shots:
+                    s.step(steps, st)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+            else:
+                with Batch(seg, shots, chunk=chunk,
+                           persistent=persistent) as bt:
+                    out.update(bt.info)
+                    bt.step(warmup, st)
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    bt.step(steps, st)
+                    e1.record(st)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1)
+            out["ms"] = ms
+            out["gpts"] = pts * steps / (ms * 1e-3) / 1e9
+            out["check_norm2"] = [float(shots[i].check()[0]) for i in (0, -1)]
+        finally:
+            for s in shots:
+                s.close()
+    return out
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
     import workloads
@@ -370,6 +450,12 @@ def run_ours(args, world, rank, local, pg):
                     "kernel_ms": kavg,
                     "steps": vs,
                 }
+            for dt in ("f32", "bf16"):
+                r = run_batch(dt)
+                variants[f"batch64_{dt}"] = {
+                    k: r[k] for k in ("gpts", "ms", "steps", "chunk",
+                                      "points", "groups", "ctas", "seed",
+                                      "autotune_s", "persistent")}
     finally:
         seg.close()
         seg1.close()
@@ -422,6 +508,24 @@ def run_ours(args, world, rank, local, pg):
                                 "cores": cores, "kind": "oracle",
                                 "sample": cpu_sample}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch_modes(args):
+    """The 64-shot workload under each schedule, one JSON line each."""
+    import torch
+    from paper_2506_02486_gb300 import buildlib
+    buildlib.build()
+    torch.cuda.set_device(0)
+    for dt in ("f32", "bf16"):
+        for name, kw in (("batch_persistent_tuned", {}),
+                         ("batch_per_step_tuned", dict(persistent=False)),
+                         ("batch_persistent_default_tile",
+                          dict(autotune=False)),
+                         ("sequential_shots_tuned", dict(sequential=True))):
+            r = run_batch(dt, **kw)
+            r["schedule"] = name
+            print(json.dumps(r), flush=True)
     return 0
 
 
@@ -514,7 +618,11 @@ def main():
     ap.add_argument("--dtype", default="f32", help="storage type for --case")
     ap.add_argument("--precision", action="store_true",
                     help="storage types vs FP64 on the 1024x1024x512 model")
+    ap.add_argument("--batch", action="store_true",
+                    help="64-shot batched workload: schedules compared")
     args = ap.parse_args()
+    if args.batch:
+        return run_batch_modes(args)
     if args.case:
         return run_case(args)
     if args.precision:

@@ -219,6 +219,12 @@ gw_status gw_domain_create(gw_ctx *ctx, const gw_shot_desc *desc, int px,
                            const int *split_y, const int *split_z,
                            int symmetric, gw_domain **out);
 gw_status gw_domain_destroy(gw_domain *d);
+/* Upper bound of the segment bytes a domain of this description takes
+ * (symmetric px x py x pz split with even extents, nrec receivers): the
+ * fields plus metadata, work items and traces.  Host only; used for
+ * admission by memory budget. */
+gw_status gw_domain_bytes(const gw_shot_desc *desc, int px, int py, int pz, int nrec,
+                          size_t *out);
 gw_status gw_domain_info_get(gw_domain *d, gw_domain_info *out);
 
 /* Velocity model (m/s), nx*ny*nz FP64 host values.  Computes vmax on the
@@ -227,6 +233,9 @@ gw_status gw_domain_info_get(gw_domain *d, gw_domain_info *out);
 gw_status gw_set_model(gw_domain *d, const double *vel_host);
 /* The same from FP32 host values. */
 gw_status gw_set_model_f32(gw_domain *d, const float *vel_host);
+/* A z-layered model: vz[z] (m/s) for every x, y of plane z (nz values,
+ * host, read during the call).  Same precompute as gw_set_model. */
+gw_status gw_set_model_layered(gw_domain *d, const double *vz);
 
 /* Ricker wavelet r(t_n) = (1 - 2 a) exp(-a), a = (pi f (n dt - 1/f))^2,
  * computed in FP64 and rounded to FP32.  Pure host function. */
@@ -344,10 +353,90 @@ gw_status gw_batch_stats_get(gw_batch *b, gw_kernel_stats *out);
  * scratch domain shaped like `desc` with a px x py x pz split (homogeneous
  * model, `steps` timed steps after a warm-up), using free segment memory,
  * and return the fastest tile (for gw_shot_desc.tile) and its time per
- * step.  Results are cached per (shape, split, storage, halo mode) for the
+ * step.  ms_all (nullable, n_all entries) receives the time per step of
+ * tile t at ms_all[t - 1] (0 for a tile that does not fit an SM).
+ * Results are cached per (shape, split, storage, halo mode, sponge) for the
  * life of the context.  Synchronises. */
 gw_status gw_autotune(gw_ctx *ctx, const gw_shot_desc *desc, int px, int py,
-                      int pz, int steps, int *best_tile, double *best_ms);
+                      int pz, int steps, int *best_tile, double *best_ms,
+                      double *ms_all, int n_all);
+/* Tiles for a batch of n single-domain shots of one storage type: each
+ * distinct shape is autotuned (as gw_autotune, cached), then one tile for
+ * every shot is chosen (the one with the least summed time) unless the
+ * per-shape best tiles are faster in sum by more than `margin` (e.g. 0.05):
+ * shots with different tiles launch one group after the other, which the
+ * per-shape timings do not see.  tiles_out[i] receives shot i's tile. */
+gw_status gw_plan_tiles(gw_ctx *ctx, int n, const gw_shot_desc *descs, int steps,
+                        double margin, int *tiles_out);
+/* Number of kernel tiles available for a storage type (GW_F32 ...). */
+gw_status gw_tile_count(int dtype, int *count);
+
+/* ------------------------------------------------------------ serving
+ * A request loop on a thread of its own: shots are submitted at any time,
+ * admitted in arrival order while their footprint (gw_domain_bytes) fits
+ * the HBM budget and a slot is free, kept resident, and advanced together
+ * in multi-shot batches (one per storage type) whose membership changes at
+ * chunk boundaries: a shot that arrives while others run joins the next
+ * chunk, a finished shot leaves it.  A chunk never runs past the end of a
+ * member shot, so each shot takes exactly its own steps and its results
+ * are those of the same shot run alone.  The segment of `ctx` must hold
+ * the budget plus the batch tables; the caller keeps it attached for the
+ * server's life. */
+typedef struct gw_server gw_server;
+
+typedef struct gw_request {
+    gw_shot_desc desc;     /* one single-domain shot of desc.nsteps steps  */
+    const float *vel;      /* nz*ny*nx host velocities (m/s), read when the
+                              shot is admitted: the caller keeps it valid
+                              until the ticket completes; or NULL and vz  */
+    const double *vz;      /* nz velocities of a z-layered model; copied
+                              by gw_submit                                 */
+    int src[3];            /* Ricker source cell (x, y, z)                 */
+    double f_peak;         /* Ricker peak frequency, Hz                    */
+    int nrec;              /* receivers, nrec x (x, y, z) in rec, copied   */
+    const int *rec;
+    float *traces;         /* host [nrec][nsteps], written before the
+                              ticket completes; NULL: not returned         */
+} gw_request;
+
+typedef struct gw_result {
+    int status;            /* GW_OK or the error that ended the shot       */
+    int steps;
+    long long points;      /* interior points                              */
+    double submit_s;       /* server clock (s since gw_server_create)      */
+    double admit_s;
+    double done_s;         /* traces on the host                           */
+    double norm2;          /* gw_check of the final state                  */
+    double energy;
+    size_t device_bytes;   /* footprint charged against the budget         */
+    int tile;
+} gw_result;
+
+typedef struct gw_server_stats {
+    int pending, active, completed, max_active;
+    int chunks;            /* chunk launches so far                        */
+    int rebuilds;          /* batch rebuilds (membership changes)          */
+    size_t budget_bytes, used_bytes, peak_bytes;
+    long long point_updates;
+    double busy_s;         /* time with at least one shot active           */
+    double now_s;          /* server clock                                 */
+} gw_server_stats;
+
+/* max_slots: most shots resident at once; chunk: steps per batch chunk
+ * (0: 25).  The server uses a non-blocking stream of its own. */
+gw_status gw_server_create(gw_ctx *ctx, size_t hbm_budget, int max_slots, int chunk,
+                           gw_server **out);
+/* Stops the loop after the running chunk; shots not finished end with
+ * GW_ERR_STATE. */
+gw_status gw_server_destroy(gw_server *s);
+/* GW_ERR_BUDGET if the shot's footprint exceeds the whole budget. */
+gw_status gw_submit(gw_server *s, const gw_request *req, uint64_t *ticket);
+/* Wait up to timeout_ms (< 0: forever) for a ticket; GW_ERR_TIMEOUT if it
+ * has not completed.  A completed ticket is returned once. */
+gw_status gw_wait(gw_server *s, uint64_t ticket, int timeout_ms, gw_result *out);
+gw_status gw_server_stats_get(gw_server *s, gw_server_stats *out);
+/* Server clock in seconds (the clock of gw_result). */
+double gw_server_now(gw_server *s);
 
 /* Record the device time of every step-kernel launch (CUDA events) while
  * enabled; gw_kernel_stats_get returns the totals and resets them. */

@@ -80,8 +80,9 @@ __global__ void k_coef(ModelSlab m, SubDev sd, int xo)
         int x = (int)(i % sd.nx);
         int y = (int)((i / sd.nx) % sd.ny);
         int gz = zl + (int)(i / npl);
-        size_t src = ((size_t)(gz - m.z_lo) * m.NY + (size_t)(sd.gy0 + y)) * m.NX +
-                     (size_t)(sd.gx0 + x);
+        size_t src = m.layered ? (size_t)(gz - m.z_lo)
+                               : ((size_t)(gz - m.z_lo) * m.NY + (size_t)(sd.gy0 + y)) * m.NX +
+                                     (size_t)(sd.gx0 + x);
         double nu = (double)v[src] * m.dt_over_h;   // FP64 precompute
         c[pidx(sd, xo, x, y, gz - sd.gz0)] = from_d<CT>(nu * nu);
     }
@@ -277,23 +278,24 @@ cudaError_t launch_chunk_end(const ShotDev *shots_dev, int nshots,
 
 // ---------------------------------------------------------------- checks
 
+// One block per interior plane z of a subdomain: (sum u^2, sum (u - up)^2
+// / coef, sum u lap(up)) of the plane to part[3 z .. 3 z + 2], summed in a
+// fixed order (no atomics), so that a check is reproducible bit for bit.
 template <class T, class CT>
-__global__ void k_check(SubDev sd, int cur, int xo, double isu, double *out)
+__global__ void k_check(SubDev sd, int cur, int xo, double isu, double *part)
 {
     const double c[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0,
                          -1.0 / 560.0};
     const T *un = reinterpret_cast<const T *>(sd.u[cur]);
     const T *up = reinterpret_cast<const T *>(sd.u[cur ^ 1]);
     const CT *cf = reinterpret_cast<const CT *>(sd.coef);
-    size_t npl = (size_t)sd.nx * sd.ny;
-    size_t n = npl * sd.nz;
+    const int z = blockIdx.x;
+    const int npl = sd.nx * sd.ny;
     double a0 = 0, a1 = 0, a2 = 0;
     const long long sx = 1, sy = sd.px, sz = (long long)sd.px * sd.py;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        int x = (int)(i % sd.nx);
-        int y = (int)((i / sd.nx) % sd.ny);
-        int z = (int)(i / npl);
+    for (int i = threadIdx.x; i < npl; i += blockDim.x) {
+        int x = i % sd.nx;
+        int y = i / sd.nx;
         size_t p = pidx(sd, xo, x, y, z);
         double u = to_d<T>(un[p]) * isu;
         double v = to_d<T>(up[p]) * isu;
@@ -307,32 +309,56 @@ __global__ void k_check(SubDev sd, int cur, int xo, double isu, double *out)
         a1 += d * d / to_d<CT>(cf[p]);
         a2 += u * lap;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    __shared__ double red[3][256];
+    red[0][threadIdx.x] = a0;
+    red[1][threadIdx.x] = a1;
+    red[2][threadIdx.x] = a2;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
+        __syncthreads();
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(out + 0, a0);
-        atomicAdd(out + 1, a1);
-        atomicAdd(out + 2, a2);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) part[3 * z + k] = red[k][0];
+}
+
+__global__ void k_check_sum(const double *part, int nplanes, double *out)
+{
+    __shared__ double red[3][256];
+    double a[3] = {0, 0, 0};
+    for (int z = threadIdx.x; z < nplanes; z += blockDim.x)
+        for (int k = 0; k < 3; ++k) a[k] += part[3 * z + k];
+    for (int k = 0; k < 3; ++k) red[k][threadIdx.x] = a[k];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
+        __syncthreads();
     }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) out[k] = red[k][0];
 }
 
 cudaError_t launch_check(const SubDev &sd, int cur, int dtype, double scale_u,
-                         double *out, cudaStream_t s)
+                         double *part, cudaStream_t s)
 {
-    size_t n = (size_t)sd.nx * sd.ny * sd.nz;
-    int g = grid_for(n);
-    int xo = dtype_xoff(dtype);
-    double isu = 1.0 / scale_u;
+    const int g = sd.nz;
+    const int xo = dtype_xoff(dtype);
+    const double isu = 1.0 / scale_u;
     switch (dtype) {
-    case DT_F32: k_check<float, float><<<g, 256, 0, s>>>(sd, cur, xo, isu, out); break;
-    case DT_F64: k_check<double, double><<<g, 256, 0, s>>>(sd, cur, xo, isu, out); break;
-    case DT_F16S: k_check<__half, __half><<<g, 256, 0, s>>>(sd, cur, xo, isu, out); break;
-    case DT_BF16: k_check<__nv_bfloat16, __half><<<g, 256, 0, s>>>(sd, cur, xo, isu, out); break;
+    case DT_F32: k_check<float, float><<<g, 256, 0, s>>>(sd, cur, xo, isu, part); break;
+    case DT_F64: k_check<double, double><<<g, 256, 0, s>>>(sd, cur, xo, isu, part); break;
+    case DT_F16S: k_check<__half, __half><<<g, 256, 0, s>>>(sd, cur, xo, isu, part); break;
+    case DT_BF16: k_check<__nv_bfloat16, __half><<<g, 256, 0, s>>>(sd, cur, xo, isu, part); break;
     default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_sum(const double *part, int nplanes, double *out, cudaStream_t s)
+{
+    k_check_sum<<<1, 256, 0, s>>>(part, nplanes, out);
     return cudaGetLastError();
 }
 

@@ -115,6 +115,8 @@ gw_status build_group(gw_batch *b, Group &g)
         off += bytes;
     }
     GW_TRY_CUDA(cudaMemset(g.d_gbar, 0, sizeof(unsigned)));
+    // the tables are in place before any launch on a non-blocking stream
+    GW_TRY_CUDA(cudaStreamSynchronize(nullptr));
     g.err = g.doms[0]->d_err;
     return GW_OK;
 }
@@ -366,58 +368,96 @@ gw_status gw_batch_stats_get(gw_batch *b, gw_kernel_stats *out)
 
 }  // extern "C"
 
-extern "C" gw_status gw_autotune(gw_ctx *c, const gw_shot_desc *desc, int px, int py,
-                                 int pz, int steps, int *best_tile, double *best_ms)
+extern "C" gw_status gw_tile_count(int dtype, int *count)
 {
-    if (!c || !desc || !best_tile || steps <= 0) return fail(GW_ERR_ARG, "bad autotune arguments");
+    if (!count || dtype < 0 || dtype > 3) return fail(GW_ERR_ARG, "bad storage type");
+    *count = step_cfg_count(dtype);
+    return GW_OK;
+}
+
+extern "C" gw_status gw_autotune(gw_ctx *c, const gw_shot_desc *desc, int px, int py,
+                                 int pz, int steps, int *best_tile, double *best_ms,
+                                 double *ms_all, int n_all)
+{
+    if (!c || !desc || !best_tile || steps <= 0 || n_all < 0 || (n_all > 0 && !ms_all))
+        return fail(GW_ERR_ARG, "bad autotune arguments");
+    if (desc->dtype < 0 || desc->dtype > 3) return fail(GW_ERR_ARG, "bad storage type");
     if (c->device < 0) return fail(GW_ERR_STATE, "autotuning needs a device context");
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     char key[160];
     std::snprintf(key, sizeof key, "%d,%d,%d|%d,%d,%d|%d|%d|%d", desc->nx, desc->ny, desc->nz,
                   px, py, pz, desc->dtype, desc->halo_mode, desc->sponge > 0);
-    auto hit = c->tuned.find(key);
-    if (hit != c->tuned.end()) {
-        *best_tile = hit->second.first;
-        if (best_ms) *best_ms = hit->second.second;
-        return GW_OK;
-    }
-    const int warm = 3;
-    gw_shot_desc dd = *desc;
-    dd.nsteps = warm + steps;
-    dd.persistent = 0;
-    dd.dt = 0;
-    const size_t npts = (size_t)desc->nx * desc->ny * desc->nz;
-    std::vector<float> vel(npts, 2000.0f);
-    int best = 0;
-    double bms = 0;
     const int ncfg = step_cfg_count(desc->dtype);
-    for (int t = 1; t <= ncfg; ++t) {
-        dd.tile = t;
-        gw_domain *d = nullptr;
-        gw_status st = gw_domain_create(c, &dd, px, py, pz, nullptr, nullptr, nullptr, 1, &d);
-        if (st != GW_OK) {
-            // a tile whose kernel does not fit an SM is skipped; anything
-            // else (memory, arguments) is the caller's problem
-            if (st == GW_ERR_CUDA && std::strstr(gw_last_error(), "does not fit")) continue;
-            return st;
+    auto hit = c->tuned.find(key);
+    if (hit == c->tuned.end()) {
+        const int warm = 3;
+        gw_shot_desc dd = *desc;
+        dd.nsteps = warm + steps;
+        dd.persistent = 0;
+        dd.dt = 0;
+        const size_t npts = (size_t)desc->nx * desc->ny * desc->nz;
+        std::vector<float> vel(npts, 2000.0f);
+        std::vector<double> times(ncfg, 0.0);
+        for (int t = 1; t <= ncfg; ++t) {
+            dd.tile = t;
+            gw_domain *d = nullptr;
+            gw_status st = gw_domain_create(c, &dd, px, py, pz, nullptr, nullptr, nullptr, 1, &d);
+            if (st != GW_OK) {
+                // a tile whose kernel does not fit an SM is skipped; anything
+                // else (memory, arguments) is the caller's problem
+                if (st == GW_ERR_CUDA && std::strstr(gw_last_error(), "does not fit")) continue;
+                return st;
+            }
+            gw_kernel_stats ks{};
+            st = gw_set_model_f32(d, vel.data());
+            if (st == GW_OK) st = gw_step(d, warm, nullptr);
+            if (st == GW_OK) st = gw_kernel_timing(d, 1);
+            if (st == GW_OK) st = gw_step(d, steps, nullptr);
+            if (st == GW_OK) st = gw_kernel_stats_get(d, &ks);
+            gw_domain_destroy(d);
+            if (st != GW_OK) return st;
+            times[t - 1] = (ks.total_ms + ks.halo_ms) / std::max(1, ks.launches);
         }
-        gw_kernel_stats ks{};
-        st = gw_set_model_f32(d, vel.data());
-        if (st == GW_OK) st = gw_step(d, warm, nullptr);
-        if (st == GW_OK) st = gw_kernel_timing(d, 1);
-        if (st == GW_OK) st = gw_step(d, steps, nullptr);
-        if (st == GW_OK) st = gw_kernel_stats_get(d, &ks);
-        gw_domain_destroy(d);
-        if (st != GW_OK) return st;
-        const double ms = (ks.total_ms + ks.halo_ms) / std::max(1, ks.launches);
-        if (best == 0 || ms < bms) {
-            best = t;
-            bms = ms;
+        hit = c->tuned.emplace(key, times).first;
+    }
+    const std::vector<double> &times = hit->second;
+    int best = 0;
+    for (int t = 1; t <= ncfg; ++t)
+        if (times[t - 1] > 0 && (best == 0 || times[t - 1] < times[best - 1])) best = t;
+    if (best == 0) return fail(GW_ERR_CUDA, "no kernel tile fits an SM");
+    *best_tile = best;
+    if (best_ms) *best_ms = times[best - 1];
+    for (int t = 0; t < n_all; ++t) ms_all[t] = t < ncfg ? times[t] : 0.0;
+    return GW_OK;
+}
+
+extern "C" gw_status gw_plan_tiles(gw_ctx *c, int n, const gw_shot_desc *descs, int steps,
+                                   double margin, int *tiles_out)
+{
+    if (!c || n <= 0 || !descs || !tiles_out || margin < 0)
+        return fail(GW_ERR_ARG, "bad tile-planning arguments");
+    const int dtype = descs[0].dtype;
+    if (dtype < 0 || dtype > 3) return fail(GW_ERR_ARG, "bad storage type");
+    const int ncfg = step_cfg_count(dtype);
+    std::vector<double> sum(ncfg, 0.0), times(ncfg);
+    std::vector<bool> ok(ncfg, true);
+    double mixed = 0;
+    for (int i = 0; i < n; ++i) {
+        if (descs[i].dtype != dtype) return fail(GW_ERR_ARG, "shots must share one storage type");
+        int best = 0;
+        double bms = 0;
+        GW_TRY(gw_autotune(c, &descs[i], 1, 1, 1, steps, &best, &bms, times.data(), ncfg));
+        tiles_out[i] = best;
+        mixed += bms;
+        for (int t = 0; t < ncfg; ++t) {
+            if (times[t] <= 0) ok[t] = false;
+            sum[t] += times[t];
         }
     }
-    if (best == 0) return fail(GW_ERR_CUDA, "no kernel tile fits an SM");
-    c->tuned[key] = {best, bms};
-    *best_tile = best;
-    if (best_ms) *best_ms = bms;
+    int uni = -1;
+    for (int t = 0; t < ncfg; ++t)
+        if (ok[t] && (uni < 0 || sum[t] < sum[uni])) uni = t;
+    if (uni >= 0 && mixed >= (1.0 - margin) * sum[uni])
+        for (int i = 0; i < n; ++i) tiles_out[i] = uni + 1;
     return GW_OK;
 }

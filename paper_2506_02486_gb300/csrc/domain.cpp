@@ -87,7 +87,13 @@ gw_status fetch_err(gw_domain *d)
 gw_status sync_dom(gw_domain *d)
 {
     GW_TRY_CUDA(cudaSetDevice(d->ctx->device));
-    GW_TRY_CUDA(cudaDeviceSynchronize());
+    if (d->step == 0 && !d->last) {
+        // never stepped: only its own setup work (legacy stream) can be in
+        // flight; other shots' launches on other streams keep running
+        GW_TRY_CUDA(cudaStreamSynchronize(nullptr));
+    } else {
+        GW_TRY_CUDA(cudaDeviceSynchronize());
+    }
     return fetch_err(d);
 }
 
@@ -186,9 +192,13 @@ gw_status plan_schedule(gw_domain *d)
     return GW_OK;
 }
 
+// Every setup call ends here: the legacy-stream copies and kernels of the
+// setup are complete when it returns, so that launches on non-blocking
+// streams (which do not wait for the legacy stream) see them.
 gw_status push_shot(gw_domain *d)
 {
     GW_TRY_CUDA(cudaMemcpy(d->d_shot, &d->shot, sizeof(ShotDev), cudaMemcpyHostToDevice));
+    GW_TRY_CUDA(cudaStreamSynchronize(nullptr));
     return GW_OK;
 }
 
@@ -605,7 +615,10 @@ gw_status gw_domain_create(gw_ctx *c, const gw_shot_desc *desc, int px, int py,
     size_t off_g = align_up(off_norm + sizeof(double) * (size_t)cap, kAlign);
     size_t off_src = align_up(off_g + sizeof(double) * (size_t)(D.nx + D.ny + D.nz), kAlign);
     size_t off_halo = align_up(off_src + sizeof(int4) * kMaxSources, kAlign);
-    size_t total = align_up(off_halo + sizeof(HaloDesc) * 6 * (size_t)nsub, kAlign);
+    size_t off_chk = align_up(off_halo + sizeof(HaloDesc) * 6 * (size_t)nsub, kAlign);
+    size_t planes = 0;
+    for (const SubDev &s : d->subs) planes += (size_t)s.nz;
+    size_t total = align_up(off_chk + 3 * sizeof(double) * planes, kAlign);
     char *m = nullptr;
     gw_status st = local_alloc(d, total, &m);
     if (st != GW_OK) return fail_out(st);
@@ -623,6 +636,7 @@ gw_status gw_domain_create(gw_ctx *c, const gw_shot_desc *desc, int px, int py,
     d->d_gtab = reinterpret_cast<double *>(m + off_g);
     d->d_src = reinterpret_cast<int4 *>(m + off_src);
     d->d_halo = reinterpret_cast<HaloDesc *>(m + off_halo);
+    d->d_chk = reinterpret_cast<double *>(m + off_chk);
 
     // sponge tables on global coordinates, FP64 (the kernels round them to
     // their arithmetic type when they load them)
@@ -707,6 +721,21 @@ gw_status gw_domain_info_get(gw_domain *d, gw_domain_info *out)
 
 static void choose_scales(gw_domain *d);
 
+// dt from the model's largest velocity (fixed dt, Courant number, or half
+// the stability limit), and the Courant number that results.
+static void set_time_step(gw_domain *d, double vmax)
+{
+    const gw_shot_desc &D = d->desc;
+    d->vmax = vmax;
+    if (D.dt > 0) {
+        d->dt = D.dt;
+    } else {
+        double nu = D.courant > 0 ? D.courant : 0.5 * nu_limit();
+        d->dt = nu * D.h / vmax;
+    }
+    d->courant = vmax * d->dt / D.h;
+}
+
 static gw_status set_model_impl(gw_domain *d, const void *vel, bool f32)
 {
     GW_TRY(check_dom(d));
@@ -735,24 +764,44 @@ static gw_status set_model_impl(gw_domain *d, const void *vel, bool f32)
     std::memcpy(&vmax, &bits, sizeof vmax);
     if (!(vmax > 0) || !std::isfinite(vmax))
         return fail(GW_ERR_ARG, "velocity model must be positive and finite");
-    d->vmax = vmax;
-    if (D.dt > 0) {
-        d->dt = D.dt;
-    } else {
-        double nu = D.courant > 0 ? D.courant : 0.5 * nu_limit();
-        d->dt = nu * D.h / vmax;
-    }
-    d->courant = vmax * d->dt / D.h;
+    set_time_step(d, vmax);
     // pass 2: coef = (v dt / h)^2 in FP64 on the GPU, rounded to storage
     for (int z = 0; z < D.nz; z += pps) {
         int zh = std::min(D.nz, z + pps);
         size_t b = plane * (size_t)(zh - z) * vs;
         GW_TRY_CUDA(cudaMemcpy(st.p, h + plane * (size_t)z * vs, b, cudaMemcpyHostToDevice));
-        ModelSlab ms{st.p, f32 ? 1 : 0, D.nx, D.ny, z, zh, d->dt / D.h};
+        ModelSlab ms{st.p, f32 ? 1 : 0, D.nx, D.ny, z, zh, d->dt / D.h, 0};
         for (const SubDev &s : d->subs)
             GW_TRY_CUDA(launch_coef(ms, s, d->dtype, nullptr));
     }
-    GW_TRY_CUDA(cudaDeviceSynchronize());
+    // the legacy stream only: work of other shots on other streams runs on
+    GW_TRY_CUDA(cudaStreamSynchronize(nullptr));
+    d->model_set = true;
+    choose_scales(d);
+    return push_shot(d);
+}
+
+gw_status gw_set_model_layered(gw_domain *d, const double *vz)
+{
+    GW_TRY(check_dom(d));
+    if (!vz) return fail(GW_ERR_ARG, "vz is NULL");
+    const gw_shot_desc &D = d->desc;
+    double vmax = 0;
+    for (int z = 0; z < D.nz; ++z) {
+        if (!(vz[z] > 0) || !std::isfinite(vz[z]))
+            return fail(GW_ERR_ARG, "velocity model must be positive and finite");
+        vmax = std::max(vmax, vz[z]);
+    }
+    std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
+    GW_TRY(sync_dom(d));
+    Stage st;
+    GW_TRY(stage_alloc(d, st, sizeof(double) * D.nz + 16, sizeof(double) * D.nz));
+    set_time_step(d, vmax);
+    GW_TRY_CUDA(cudaMemcpy(st.p, vz, sizeof(double) * D.nz, cudaMemcpyHostToDevice));
+    ModelSlab ms{st.p, 0, D.nx, D.ny, 0, D.nz, d->dt / D.h, 1};
+    for (const SubDev &s : d->subs)
+        GW_TRY_CUDA(launch_coef(ms, s, d->dtype, nullptr));
+    GW_TRY_CUDA(cudaStreamSynchronize(nullptr));
     d->model_set = true;
     choose_scales(d);
     return push_shot(d);
@@ -1047,9 +1096,13 @@ gw_status gw_check(gw_domain *d, double *norm2, double *energy)
     GW_TRY(check_dom(d));
     std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
     GW_TRY(sync_dom(d));
-    GW_TRY_CUDA(cudaMemset(d->d_scratch, 0, 3 * sizeof(double)));
-    for (const SubDev &s : d->subs)
-        GW_TRY_CUDA(launch_check(s, d->step & 1, d->dtype, d->su, d->d_scratch, nullptr));
+    int planes = 0;
+    for (const SubDev &s : d->subs) {
+        GW_TRY_CUDA(launch_check(s, d->step & 1, d->dtype, d->su, d->d_chk + 3 * planes,
+                                 nullptr));
+        planes += s.nz;
+    }
+    GW_TRY_CUDA(launch_check_sum(d->d_chk, planes, d->d_scratch, nullptr));
     double a[3];
     GW_TRY_CUDA(cudaMemcpy(a, d->d_scratch, sizeof a, cudaMemcpyDeviceToHost));
     if (norm2) *norm2 = a[0];
@@ -1140,3 +1193,46 @@ gw_status gw_load_state(gw_domain *d, const void *in)
 }
 
 }  // extern "C"
+
+extern "C" gw_status gw_domain_bytes(const gw_shot_desc *desc, int px, int py, int pz,
+                                     int nrec, size_t *out)
+{
+    if (!desc || !out || px <= 0 || py <= 0 || pz <= 0 || nrec < 0)
+        return fail(GW_ERR_ARG, "bad arguments");
+    const gw_shot_desc &D = *desc;
+    if (D.nx <= 0 || D.ny <= 0 || D.nz <= 0 || D.dtype < DT_F32 || D.dtype > DT_BF16)
+        return fail(GW_ERR_ARG, "bad grid or storage type");
+    const bool delta = D.dtype == DT_F16S || D.dtype == DT_BF16;
+    const int es = dtype_size(D.dtype), xo = dtype_xoff(D.dtype);
+    const size_t nsub = (size_t)px * py * pz;
+    // symmetric layout: every subdomain padded like the largest one
+    const int lx = (D.nx + px - 1) / px, ly = (D.ny + py - 1) / py, lz = (D.nz + pz - 1) / pz;
+    const size_t pitch = align_up((size_t)(xo + lx + R), (size_t)(128 / es));
+    const size_t elems = pitch * (size_t)(ly + 2 * R) * (size_t)(lz + 2 * R);
+    // u0, u1 (and w in the delta form) in the storage type, coef in FP16
+    // for the 16-bit types
+    size_t total = (delta ? 3 : 2) * align_up(elems * es, kAlign) * nsub;
+    total += align_up(elems * (delta ? 2 : es), kAlign) * nsub;
+    // metadata, tensor maps, tables (as laid out by gw_domain_create)
+    const size_t cap = (size_t)std::max(1, D.nsteps);
+    total += align_up(sizeof(SubDev) * nsub, kAlign) + 2 * kAlign +
+             align_up(128 * kMapsPerSub * nsub, kAlign) + kAlign +
+             align_up(sizeof(double) * kMaxSources * cap, kAlign) +
+             align_up(sizeof(double) * cap, kAlign) +
+             align_up(sizeof(double) * (size_t)(D.nx + D.ny + D.nz), kAlign) +
+             align_up(sizeof(int4) * kMaxSources, kAlign) +
+             align_up(sizeof(HaloDesc) * 6 * nsub, kAlign) +
+             align_up(3 * sizeof(double) * (size_t)lz * nsub, kAlign);
+    // work items and one chunk of norm partials, bounded with the smallest
+    // tile extents (32 x 7) and items of at least 32 planes
+    const size_t chunk = D.chunk == 0 ? kDefaultChunk : (size_t)std::max(1, std::abs(D.chunk));
+    const size_t items = nsub * (size_t)((lx + 31) / 32) * (size_t)((ly + 6) / 7) *
+                         (size_t)std::max(1, lz / 32);
+    total += align_up((sizeof(Item) + sizeof(double) * chunk) * items + kAlign, kAlign);
+    // receivers and their traces
+    if (nrec)
+        total += align_up(sizeof(int4) * nrec, kAlign) +
+                 align_up(sizeof(float) * (size_t)nrec * cap, kAlign);
+    *out = total;
+    return GW_OK;
+}

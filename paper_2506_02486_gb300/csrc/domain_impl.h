@@ -44,6 +44,7 @@ struct gw_domain {
     int *d_step = nullptr;
     unsigned *d_gbar = nullptr;           // barrier of persistent launches
     double *d_scratch = nullptr;          // 4 doubles for checks
+    double *d_chk = nullptr;              // 3 per-plane check partials per z
     double *d_wavelet = nullptr;
     double *d_norms = nullptr;
     double *d_gtab = nullptr;             // gx | gy | gz

@@ -87,8 +87,8 @@ struct gw_ctx {
     std::vector<cudaStream_t> put_streams;
     std::recursive_mutex mu;
     int num_sms = 0;
-    // autotuner results: shape/split/type key -> (tile, ms per step)
-    std::map<std::string, std::pair<int, double>> tuned;
+    // autotuner results: shape/split/type key -> time per step of each tile
+    std::map<std::string, std::vector<double>> tuned;   // ms per tile
 
     char *rank_base(int r) const { return base + (size_t)r * rank_bytes; }
 };

@@ -47,6 +47,7 @@ struct ModelSlab {
     int NX, NY;        // global x, y extents
     int z_lo, z_hi;    // global planes in the slab
     double dt_over_h;
+    int layered;       // 1: v holds one value per plane (v[z - z_lo])
 };
 cudaError_t launch_coef(const ModelSlab &m, const SubDev &sub, int dtype,
                         cudaStream_t s);
@@ -91,9 +92,13 @@ cudaError_t launch_chunk_end(const ShotDev *shots_dev, int nshots,
 
 // FP64 check reductions over subdomain `sub` of a shot's current state
 // (cur = index of the buffer holding u_n; the other holds u_{n-1}):
-// out[0] += sum u_n^2, out[1] += sum (u_n - u_{n-1})^2 / coef,
-// out[2] += sum u_n lap(u_{n-1}); u unscaled by 1/scale_u.
+// Per interior plane z of `sub`: part[3z] = sum u_n^2, part[3z+1] =
+// sum (u_n - u_{n-1})^2 / coef, part[3z+2] = sum u_n lap(u_{n-1}); u
+// unscaled by 1/scale_u.  launch_check_sum adds nplanes such triples in a
+// fixed order into out[0..2].
 cudaError_t launch_check(const SubDev &sub, int cur, int dtype,
-                         double scale_u, double *out, cudaStream_t s);
+                         double scale_u, double *part, cudaStream_t s);
+cudaError_t launch_check_sum(const double *part, int nplanes, double *out,
+                             cudaStream_t s);
 
 }  // namespace gw

@@ -1,0 +1,413 @@
+// server.cpp -- continuous-batching shot server.  One loop thread owns all
+// GPU work: it admits submitted shots in arrival order while they fit the
+// HBM budget and a slot, sets them up (legacy-stream copies, overlapped
+// with the running chunk), advances every resident shot with one multi-shot
+// batch per storage type on its own non-blocking stream, and retires shots
+// at chunk boundaries (traces to the caller's buffer, final check).
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+
+#include "domain_impl.h"
+
+using namespace gw;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+    uint64_t ticket = 0;
+    gw_request r{};
+    std::vector<double> vz;      // owned copy of a layered model
+    std::vector<int> rec;        // owned copy of the receivers
+    size_t bytes = 0;            // footprint charged against the budget
+    long long points = 0;
+    gw_result res{};
+    gw_domain *dom = nullptr;
+    int left = 0;                // steps still to take
+};
+
+}  // namespace
+
+struct gw_server {
+    gw_ctx *ctx = nullptr;
+    size_t budget = 0;
+    int slots = 0;
+    int chunk = kDefaultChunk;
+    cudaStream_t stream = nullptr;
+    Clock::time_point t0;
+    std::thread th;
+
+    // shared with the callers, under mu
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req *> pending;
+    std::unordered_map<uint64_t, Req *> live;   // pending or active
+    std::unordered_map<uint64_t, Req *> done;   // completed, not yet waited
+    uint64_t next = 1;
+    bool stop = false;
+    bool blocked = false;        // the head did not fit the segment: wait for a retirement
+    size_t used = 0;
+    gw_server_stats st{};
+
+    // loop thread only
+    std::vector<Req *> active;
+    gw_batch *batch[4] = {nullptr, nullptr, nullptr, nullptr};
+
+    double now() const
+    {
+        return std::chrono::duration<double>(Clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+// Pop the admissible prefix of the queue (arrival order: a shot that does
+// not fit holds back the ones behind it, so large shots are not starved).
+void take_admissible(gw_server *S, std::vector<Req *> &out)
+{
+    while (!S->pending.empty() && !S->blocked) {
+        Req *q = S->pending.front();
+        const int resident = (int)(S->active.size() + out.size());
+        if (resident >= S->slots || S->used + q->bytes > S->budget) break;
+        S->pending.pop_front();
+        S->used += q->bytes;
+        S->st.peak_bytes = std::max(S->st.peak_bytes, S->used);
+        out.push_back(q);
+    }
+}
+
+void finish(gw_server *S, Req *q, gw_status status)
+{
+    if (q->dom) {
+        gw_domain_destroy(q->dom);
+        q->dom = nullptr;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    q->res.status = status;
+    q->res.done_s = S->now();
+    S->used -= q->bytes;
+    S->live.erase(q->ticket);
+    S->done[q->ticket] = q;
+    S->st.completed++;
+    S->blocked = false;
+    S->cv_done.notify_all();
+}
+
+// Create the shot's domain and load its model, source and receivers.
+gw_status setup(gw_server *S, Req *q)
+{
+    q->res.admit_s = S->now();
+    gw_shot_desc d = q->r.desc;
+    GW_TRY(gw_domain_create(S->ctx, &d, 1, 1, 1, nullptr, nullptr, nullptr, 1, &q->dom));
+    if (q->r.vel) GW_TRY(gw_set_model_f32(q->dom, q->r.vel));
+    else GW_TRY(gw_set_model_layered(q->dom, q->vz.data()));
+    GW_TRY(gw_inject_ricker(q->dom, q->r.src[0], q->r.src[1], q->r.src[2], q->r.f_peak));
+    if (q->r.nrec) GW_TRY(gw_set_receivers(q->dom, q->r.nrec, q->rec.data()));
+    q->res.tile = q->dom->cfg + 1;
+    q->left = d.nsteps;
+    return GW_OK;
+}
+
+// Set up newly admitted shots; those that cannot be placed in the segment
+// (fragmentation) go back to the head of the queue while others are
+// resident.  Returns the shots ready to join.
+std::vector<Req *> setup_all(gw_server *S, std::vector<Req *> &adm, bool others_resident)
+{
+    std::vector<Req *> ready;
+    for (size_t i = 0; i < adm.size(); ++i) {
+        Req *q = adm[i];
+        gw_status st = setup(S, q);
+        if (st == GW_OK) {
+            ready.push_back(q);
+            continue;
+        }
+        if (q->dom) {
+            gw_domain_destroy(q->dom);
+            q->dom = nullptr;
+        }
+        if (st == GW_ERR_BUDGET && (others_resident || !ready.empty())) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            // this one and every later admission go back, in order
+            for (size_t j = adm.size(); j-- > i;) {
+                if (adm[j]->dom) {
+                    gw_domain_destroy(adm[j]->dom);
+                    adm[j]->dom = nullptr;
+                }
+                S->pending.push_front(adm[j]);
+                S->used -= adm[j]->bytes;
+            }
+            S->blocked = true;
+            break;
+        }
+        finish(S, q, st);
+    }
+    adm.clear();
+    return ready;
+}
+
+gw_status rebuild(gw_server *S)
+{
+    for (gw_batch *&b : S->batch) {
+        if (b) gw_batch_destroy(b);
+        b = nullptr;
+    }
+    for (int t = 0; t < 4; ++t) {
+        std::vector<gw_domain *> doms;
+        for (Req *q : S->active)
+            if (q->r.desc.dtype == t) doms.push_back(q->dom);
+        if (doms.empty()) continue;
+        // persistent chunks without graphs: membership changes too often
+        // for captured graphs to pay off
+        GW_TRY(gw_batch_create(S->ctx, (int)doms.size(), doms.data(), -S->chunk, 1,
+                               &S->batch[t]));
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->st.rebuilds++;
+    return GW_OK;
+}
+
+void retire(gw_server *S, Req *q)
+{
+    gw_status st = GW_OK;
+    const int n = q->r.desc.nsteps;
+    if (q->r.traces && q->r.nrec)
+        st = gw_read_receivers(q->dom, q->r.traces, q->r.nrec, n);
+    if (st == GW_OK) st = gw_check(q->dom, &q->res.norm2, &q->res.energy);
+    finish(S, q, st);
+}
+
+void loop(gw_server *S)
+{
+    cudaSetDevice(S->ctx->device);
+    bool dirty = false;
+    for (;;) {
+        std::vector<Req *> adm;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (S->active.empty()) {
+                S->cv_work.wait(lk, [&] {
+                    return S->stop || (!S->pending.empty() && !S->blocked);
+                });
+            }
+            if (S->stop) break;
+            take_admissible(S, adm);
+        }
+        if (!adm.empty()) {
+            std::vector<Req *> ready = setup_all(S, adm, !S->active.empty());
+            if (!ready.empty()) {
+                S->active.insert(S->active.end(), ready.begin(), ready.end());
+                dirty = true;
+            }
+        }
+        if (S->active.empty()) continue;
+        if (dirty) {
+            gw_status st = rebuild(S);
+            if (st != GW_OK) {
+                for (Req *q : S->active) finish(S, q, st);
+                S->active.clear();
+                continue;
+            }
+            dirty = false;
+        }
+        int K = S->chunk;
+        long long pts = 0;
+        for (Req *q : S->active) {
+            K = std::min(K, q->left);
+            pts += q->points;
+        }
+        const double t_launch = S->now();
+        gw_status st = GW_OK;
+        for (gw_batch *b : S->batch)
+            if (b && st == GW_OK) st = gw_batch_step(b, K, S->stream);
+        // while the chunk runs: admit and set up the next shots
+        std::vector<Req *> joiners;
+        if (st == GW_OK) {
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                take_admissible(S, adm);
+            }
+            if (!adm.empty()) joiners = setup_all(S, adm, true);
+        }
+        cudaError_t e = cudaStreamSynchronize(S->stream);
+        if (st == GW_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->st.chunks++;
+            S->st.point_updates += pts * K;
+            S->st.busy_s += S->now() - t_launch;
+        }
+        std::vector<Req *> keep;
+        for (Req *q : S->active) {
+            if (st != GW_OK) {
+                finish(S, q, st);
+                dirty = true;
+                continue;
+            }
+            q->left -= K;
+            if (q->left > 0) {
+                keep.push_back(q);
+            } else {
+                retire(S, q);
+                dirty = true;
+            }
+        }
+        S->active.swap(keep);
+        if (!joiners.empty()) {
+            S->active.insert(S->active.end(), joiners.begin(), joiners.end());
+            dirty = true;
+        }
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->st.max_active = std::max(S->st.max_active, (int)S->active.size());
+    }
+    // stopped: nothing runs any more
+    cudaStreamSynchronize(S->stream);
+    for (gw_batch *&b : S->batch) {
+        if (b) gw_batch_destroy(b);
+        b = nullptr;
+    }
+    for (Req *q : S->active) finish(S, q, GW_ERR_STATE);
+    S->active.clear();
+    std::vector<Req *> rest;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        rest.assign(S->pending.begin(), S->pending.end());
+        S->pending.clear();
+    }
+    for (Req *q : rest) finish(S, q, GW_ERR_STATE);
+}
+
+}  // namespace
+
+extern "C" {
+
+gw_status gw_server_create(gw_ctx *c, size_t hbm_budget, int max_slots, int chunk,
+                           gw_server **out)
+{
+    if (!c || !out || hbm_budget == 0 || max_slots <= 0 || chunk < 0)
+        return fail(GW_ERR_ARG, "bad server arguments");
+    *out = nullptr;
+    if (c->device < 0) return fail(GW_ERR_STATE, "serving needs a device context");
+    if (!c->base) return fail(GW_ERR_STATE, "no segment attached");
+    if (hbm_budget > c->rank_bytes)
+        return fail(GW_ERR_BUDGET, "budget of %zu bytes exceeds the segment (%zu per rank)",
+                    hbm_budget, c->rank_bytes);
+    gw_server *S = new (std::nothrow) gw_server();
+    if (!S) return fail(GW_ERR_NOMEM, "out of host memory");
+    S->ctx = c;
+    S->budget = hbm_budget;
+    S->slots = max_slots;
+    S->chunk = chunk == 0 ? kDefaultChunk : chunk;
+    S->st.budget_bytes = hbm_budget;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete S;
+        return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    S->t0 = Clock::now();
+    try {
+        S->th = std::thread(loop, S);
+    } catch (...) {
+        cudaStreamDestroy(S->stream);
+        delete S;
+        return fail(GW_ERR_NOMEM, "cannot start the server thread");
+    }
+    *out = S;
+    return GW_OK;
+}
+
+gw_status gw_server_destroy(gw_server *S)
+{
+    if (!S) return GW_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->th.joinable()) S->th.join();
+    for (auto &kv : S->done) delete kv.second;
+    cudaStreamDestroy(S->stream);
+    delete S;
+    return GW_OK;
+}
+
+gw_status gw_submit(gw_server *S, const gw_request *req, uint64_t *ticket)
+{
+    if (!S || !req || !ticket) return fail(GW_ERR_ARG, "NULL argument");
+    const gw_shot_desc &D = req->desc;
+    if (D.nx <= 0 || D.ny <= 0 || D.nz <= 0 || D.nsteps <= 0)
+        return fail(GW_ERR_ARG, "a request needs a grid and at least one step");
+    if (!req->vel && !req->vz) return fail(GW_ERR_ARG, "a request needs vel or vz");
+    if (req->nrec < 0 || (req->nrec && !req->rec)) return fail(GW_ERR_ARG, "bad receivers");
+    size_t bytes = 0;
+    GW_TRY(gw_domain_bytes(&D, 1, 1, 1, req->nrec, &bytes));
+    if (bytes > S->budget)
+        return fail(GW_ERR_BUDGET, "shot needs %zu bytes; the budget is %zu", bytes, S->budget);
+    Req *q = new (std::nothrow) Req();
+    if (!q) return fail(GW_ERR_NOMEM, "out of host memory");
+    q->r = *req;
+    if (!req->vel) q->vz.assign(req->vz, req->vz + D.nz);
+    q->r.vz = nullptr;
+    if (req->nrec) q->rec.assign(req->rec, req->rec + 3 * (size_t)req->nrec);
+    q->r.rec = nullptr;
+    q->bytes = bytes;
+    q->points = (long long)D.nx * D.ny * D.nz;
+    q->res.steps = D.nsteps;
+    q->res.points = q->points;
+    q->res.device_bytes = bytes;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) {
+            delete q;
+            return fail(GW_ERR_STATE, "server is stopping");
+        }
+        q->ticket = S->next++;
+        q->res.submit_s = S->now();
+        S->pending.push_back(q);
+        S->live[q->ticket] = q;
+        *ticket = q->ticket;
+    }
+    S->cv_work.notify_all();
+    return GW_OK;
+}
+
+gw_status gw_wait(gw_server *S, uint64_t ticket, int timeout_ms, gw_result *out)
+{
+    if (!S || !out) return fail(GW_ERR_ARG, "NULL argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto ready = [&] { return S->done.count(ticket) || !S->live.count(ticket); };
+    if (timeout_ms < 0) {
+        S->cv_done.wait(lk, ready);
+    } else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
+        return fail(GW_ERR_TIMEOUT, "ticket %llu not complete", (unsigned long long)ticket);
+    }
+    auto it = S->done.find(ticket);
+    if (it == S->done.end())
+        return fail(GW_ERR_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    *out = it->second->res;
+    delete it->second;
+    S->done.erase(it);
+    return GW_OK;
+}
+
+gw_status gw_server_stats_get(gw_server *S, gw_server_stats *out)
+{
+    if (!S || !out) return fail(GW_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    *out = S->st;
+    out->pending = (int)S->pending.size();
+    out->active = (int)(S->live.size() - S->pending.size());
+    out->used_bytes = S->used;
+    out->now_s = S->now();
+    return GW_OK;
+}
+
+double gw_server_now(gw_server *S) { return S ? S->now() : 0.0; }
+
+}  // extern "C"

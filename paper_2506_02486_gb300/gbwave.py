@@ -72,6 +72,36 @@ class gw_kernel_stats(ctypes.Structure):
                 ("halo_ms", ctypes.c_double)]
 
 
+class gw_request(ctypes.Structure):
+    _fields_ = [
+        ("desc", gw_shot_desc), ("vel", ctypes.c_void_p),
+        ("vz", ctypes.c_void_p), ("src", ctypes.c_int * 3),
+        ("f_peak", ctypes.c_double), ("nrec", ctypes.c_int),
+        ("rec", ctypes.c_void_p), ("traces", ctypes.c_void_p),
+    ]
+
+
+class gw_result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("steps", ctypes.c_int),
+        ("points", ctypes.c_longlong), ("submit_s", ctypes.c_double),
+        ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double),
+        ("norm2", ctypes.c_double), ("energy", ctypes.c_double),
+        ("device_bytes", ctypes.c_size_t), ("tile", ctypes.c_int),
+    ]
+
+
+class gw_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("pending", ctypes.c_int), ("active", ctypes.c_int),
+        ("completed", ctypes.c_int), ("max_active", ctypes.c_int),
+        ("chunks", ctypes.c_int), ("rebuilds", ctypes.c_int),
+        ("budget_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t),
+        ("peak_bytes", ctypes.c_size_t), ("point_updates", ctypes.c_longlong),
+        ("busy_s", ctypes.c_double), ("now_s", ctypes.c_double),
+    ]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _SZ = ctypes.c_size_t
@@ -99,9 +129,12 @@ _SIGS = {
     "gw_domain_create": [_P, ctypes.POINTER(gw_shot_desc), _I, _I, _I, _P,
                          _P, _P, _I, ctypes.POINTER(_P)],
     "gw_domain_destroy": [_P],
+    "gw_domain_bytes": [ctypes.POINTER(gw_shot_desc), _I, _I, _I, _I,
+                        ctypes.POINTER(_SZ)],
     "gw_domain_info_get": [_P, ctypes.POINTER(gw_domain_info)],
     "gw_set_model": [_P, _P],
     "gw_set_model_f32": [_P, _P],
+    "gw_set_model_layered": [_P, _P],
     "gw_ricker": [_D, _D, _I, _P],
     "gw_inject_source": [_P, _I, _I, _I, _P, _I],
     "gw_inject_ricker": [_P, _I, _I, _I, _D],
@@ -125,14 +158,23 @@ _SIGS = {
     "gw_batch_timing": [_P, _I],
     "gw_batch_stats_get": [_P, ctypes.POINTER(gw_kernel_stats)],
     "gw_autotune": [_P, ctypes.POINTER(gw_shot_desc), _I, _I, _I, _I,
-                    ctypes.POINTER(_I), ctypes.POINTER(_D)],
+                    ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _I],
+    "gw_tile_count": [_I, ctypes.POINTER(_I)],
+    "gw_plan_tiles": [_P, _I, _P, _I, _D, _P],
+    "gw_server_create": [_P, _SZ, _I, _I, ctypes.POINTER(_P)],
+    "gw_server_destroy": [_P],
+    "gw_submit": [_P, ctypes.POINTER(gw_request), ctypes.POINTER(_U64)],
+    "gw_wait": [_P, _U64, _I, ctypes.POINTER(gw_result)],
+    "gw_server_stats_get": [_P, ctypes.POINTER(gw_server_stats)],
+    "gw_server_now": [_P],
     "gw_state_bytes": [_P, ctypes.POINTER(_SZ)],
     "gw_save_state": [_P, _P],
     "gw_load_state": [_P, _P],
 }
 _RESTYPES = {"gw_last_error": ctypes.c_char_p,
              "gw_status_string": ctypes.c_char_p,
-             "gw_version": ctypes.c_char_p}
+             "gw_version": ctypes.c_char_p,
+             "gw_server_now": ctypes.c_double}
 
 _lib = None
 _lock = threading.Lock()
@@ -319,6 +361,14 @@ def gw_domain_destroy(dom: int):
     _check(lib().gw_domain_destroy(dom), "gw_domain_destroy")
 
 
+def gw_domain_bytes(desc: gw_shot_desc, px=1, py=1, pz=1, nrec=0) -> int:
+    n = _SZ()
+    _check(lib().gw_domain_bytes(ctypes.byref(desc), int(px), int(py),
+                                 int(pz), int(nrec), ctypes.byref(n)),
+           "gw_domain_bytes")
+    return n.value
+
+
 def gw_domain_info_get(dom: int) -> dict:
     i = gw_domain_info()
     _check(lib().gw_domain_info_get(dom, ctypes.byref(i)),
@@ -334,6 +384,11 @@ def gw_set_model(dom: int, vel: np.ndarray):
 def gw_set_model_f32(dom: int, vel: np.ndarray):
     v = np.ascontiguousarray(vel, dtype=np.float32)
     _check(lib().gw_set_model_f32(dom, _ptr(v)), "gw_set_model_f32")
+
+
+def gw_set_model_layered(dom: int, vz: np.ndarray):
+    v = np.ascontiguousarray(vz, dtype=np.float64)
+    _check(lib().gw_set_model_layered(dom, _ptr(v)), "gw_set_model_layered")
 
 
 def gw_ricker(f_peak: float, dt: float, n: int) -> np.ndarray:
@@ -472,13 +527,76 @@ def gw_batch_stats_get(b: int) -> dict:
             "halo_ms": s.halo_ms}
 
 
+def gw_tile_count(dtype) -> int:
+    n = _I()
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    _check(lib().gw_tile_count(dt, ctypes.byref(n)), "gw_tile_count")
+    return n.value
+
+
 def gw_autotune(ctx: int, desc: gw_shot_desc, px: int = 1, py: int = 1,
-                pz: int = 1, steps: int = 10) -> tuple[int, float]:
+                pz: int = 1, steps: int = 10, all_times: bool = False):
+    """(best tile, ms per step), plus the list of every tile's ms per step
+    (0 where a tile does not fit) when all_times is set."""
+    n = gw_tile_count(desc.dtype)
     t, ms = _I(), _D()
+    times = np.zeros(n, dtype=np.float64)
     _check(lib().gw_autotune(ctx, ctypes.byref(desc), int(px), int(py),
                              int(pz), int(steps), ctypes.byref(t),
-                             ctypes.byref(ms)), "gw_autotune")
+                             ctypes.byref(ms), _ptr(times), n), "gw_autotune")
+    if all_times:
+        return t.value, ms.value, times.tolist()
     return t.value, ms.value
+
+
+def gw_plan_tiles(ctx: int, descs, steps: int = 10,
+                  margin: float = 0.05) -> list[int]:
+    arr = (gw_shot_desc * len(descs))(*descs)
+    out = np.zeros(len(descs), dtype=np.int32)
+    _check(lib().gw_plan_tiles(ctx, len(descs), ctypes.cast(arr, _P),
+                               int(steps), float(margin), _ptr(out)),
+           "gw_plan_tiles")
+    return [int(v) for v in out]
+
+
+def gw_server_create(ctx: int, hbm_budget: int, max_slots: int,
+                     chunk: int = 0) -> int:
+    h = _P()
+    _check(lib().gw_server_create(ctx, int(hbm_budget), int(max_slots),
+                                  int(chunk), ctypes.byref(h)),
+           "gw_server_create")
+    return h.value
+
+
+def gw_server_destroy(srv: int):
+    _check(lib().gw_server_destroy(srv), "gw_server_destroy")
+
+
+def gw_submit(srv: int, req: gw_request) -> int:
+    """The caller keeps req.vel and req.traces valid until the ticket
+    completes (gw_wait returned it)."""
+    t = _U64()
+    _check(lib().gw_submit(srv, ctypes.byref(req), ctypes.byref(t)),
+           "gw_submit")
+    return t.value
+
+
+def gw_wait(srv: int, ticket: int, timeout_ms: int = -1) -> dict:
+    r = gw_result()
+    _check(lib().gw_wait(srv, int(ticket), int(timeout_ms), ctypes.byref(r)),
+           "gw_wait")
+    return {k: getattr(r, k) for k, _ in gw_result._fields_}
+
+
+def gw_server_stats_get(srv: int) -> dict:
+    st = gw_server_stats()
+    _check(lib().gw_server_stats_get(srv, ctypes.byref(st)),
+           "gw_server_stats_get")
+    return {k: getattr(st, k) for k, _ in gw_server_stats._fields_}
+
+
+def gw_server_now(srv: int) -> float:
+    return float(lib().gw_server_now(srv))
 
 
 def gw_state_bytes(dom: int) -> int:

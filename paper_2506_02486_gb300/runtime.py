@@ -161,3 +161,71 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Server:
+    """Continuous-batching shot server on a segment (one loop thread in the
+    library).  Keeps each request's host buffers alive until it is
+    waited for."""
+
+    def __init__(self, seg: Segment, budget: int, max_slots: int = 64,
+                 chunk: int = 0):
+        self.seg = seg
+        self.h = gw.gw_server_create(seg.ctx, budget, max_slots, chunk)
+        self._keep = {}
+
+    def submit(self, nx, ny, nz, nsteps, *, src, f_peak=20.0, vel=None,
+               vz=None, receivers=None, dtype="f32", sponge=20, h=10.0,
+               tile=0) -> int:
+        req = gw.gw_request()
+        req.desc = gw.shot_desc(nx, ny, nz, h=h, nsteps=nsteps, dtype=dtype,
+                                sponge=sponge, tile=tile)
+        keep = []
+        if vel is not None:
+            v = np.ascontiguousarray(vel, dtype=np.float32)
+            assert v.size == nx * ny * nz
+            req.vel = v.ctypes.data
+            keep.append(v)
+        else:
+            v = np.ascontiguousarray(vz, dtype=np.float64)
+            assert v.size == nz
+            req.vz = v.ctypes.data
+            keep.append(v)
+        req.src[:] = [int(c) for c in src]
+        req.f_peak = float(f_peak)
+        traces = None
+        if receivers is not None and len(receivers):
+            r = np.ascontiguousarray(np.asarray(receivers, dtype=np.int32)
+                                     .reshape(-1, 3))
+            req.nrec = r.shape[0]
+            req.rec = r.ctypes.data
+            traces = np.zeros((r.shape[0], nsteps), dtype=np.float32)
+            req.traces = traces.ctypes.data
+            keep.append(r)
+        t = gw.gw_submit(self.h, req)
+        self._keep[t] = (keep, traces)
+        return t
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> dict:
+        res = gw.gw_wait(self.h, ticket, timeout_ms)
+        _, traces = self._keep.pop(ticket)
+        res["traces"] = traces
+        return res
+
+    def stats(self) -> dict:
+        return gw.gw_server_stats_get(self.h)
+
+    def now(self) -> float:
+        return gw.gw_server_now(self.h)
+
+    def close(self):
+        if self.h:
+            gw.gw_server_destroy(self.h)
+            self.h = 0
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -184,3 +184,49 @@ def test_domain_needs_device_context(lib):
         assert e.value.status == gw.GW_ERR_STATE
     finally:
         s.close()
+
+
+STRUCTS = ["gw_shot_desc", "gw_domain_info", "gw_kernel_stats", "gw_request",
+           "gw_result", "gw_server_stats"]
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof and offsetof of every struct the binding mirrors, from a C
+    program compiled against the header, equal the ctypes layout."""
+    lines = ["#include <stdio.h>", "#include <stddef.h>",
+             '#include "gbwave.h"', "int main(void) {"]
+    for name in STRUCTS:
+        cls = getattr(gw, name)
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True,
+                         check=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line)
+    for name in STRUCTS:
+        cls = getattr(gw, name)
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
+
+
+def test_domain_bytes_bounds_the_fields(lib):
+    """The admission footprint covers the padded fields (two wavefields and
+    coef; plus w and an FP16 coef in the delta form) and grows with the
+    step count (traces, wavelet table)."""
+    from paper_2506_02486_gb300.runtime import padded_bytes
+    for dtype, nf in (("f32", 3), ("f64", 3), ("bf16", 4), ("f16s", 4)):
+        d = gw.shot_desc(100, 90, 80, nsteps=10, dtype=dtype)
+        b = gw.gw_domain_bytes(d)
+        assert b >= nf * padded_bytes(100, 90, 80, dtype)
+        assert b < nf * padded_bytes(100, 90, 80, dtype) * 1.2 + (4 << 20)
+        d2 = gw.shot_desc(100, 90, 80, nsteps=1000, dtype=dtype)
+        assert gw.gw_domain_bytes(d2, nrec=64) > b + 64 * 990 * 4
+    with pytest.raises(gw.GWError):
+        gw.gw_domain_bytes(gw.shot_desc(0, 8, 8))

@@ -150,10 +150,20 @@ def test_autotune_picks_an_available_tile_and_caches_it():
     n = 96
     with Segment(6 * shot_bytes(n, n, n, "f32", 16)) as seg:
         d = gw.shot_desc(n, n, n, nsteps=16, sponge=10)
-        t1, ms1 = gw.gw_autotune(seg.ctx, d, 1, 1, 1, 5)
+        t1, ms1, all1 = gw.gw_autotune(seg.ctx, d, 1, 1, 1, 5, all_times=True)
         t2, ms2 = gw.gw_autotune(seg.ctx, d, 1, 1, 1, 5)
         assert t1 >= 1 and ms1 > 0
         assert (t1, ms1) == (t2, ms2)
+        assert len(all1) == gw.gw_tile_count("f32")
+        assert ms1 == min(t for t in all1 if t > 0) == all1[t1 - 1]
+        # planning: with an unreachable margin every shot gets one tile; with
+        # margin 0 each shape keeps its own best tile unless one tile is
+        # at least as fast in sum
+        d2 = gw.shot_desc(n + 16, n, n, nsteps=16, sponge=10)
+        uni = gw.gw_plan_tiles(seg.ctx, [d, d2, d], 5, margin=1.0)
+        assert len(set(uni)) == 1
+        own = gw.gw_plan_tiles(seg.ctx, [d, d2], 5, margin=0.0)
+        assert own[0] == t1 or len(set(own)) == 1
         # the chosen tile builds and runs
         with Shot(seg, n, n, n, nsteps=16, sponge=10, tile=t1) as s:
             s.set_model(workloads.homogeneous(n, n, n))

@@ -36,6 +36,7 @@ import numpy as np
 __all__ = [
     "homogeneous",
     "layered",
+    "layered_profile",
     "perturbed",
     "random_field",
     "source_position",
@@ -69,6 +70,13 @@ def layered(nx: int, ny: int, nz: int, seed: int, nlayers: int = 8,
     out = np.empty((nz, ny, nx), dtype=np.float64)
     out[...] = prof[:, None, None]
     return out
+
+
+def layered_profile(nz: int, seed: int, nlayers: int = 8,
+                    vmin: float = 1500.0, vmax: float = 4500.0) -> np.ndarray:
+    """The z profile of ``layered`` with the same seed (nz values)."""
+    rng = np.random.default_rng(seed)
+    return _layer_profile(nz, rng, nlayers, vmin, vmax)
 
 
 def perturbed(base: np.ndarray, seed: int, sigma: float = 0.05,
