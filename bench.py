@@ -511,6 +511,79 @@ def run_ours(args, world, rank, local, pg):
     return 0
 
 
+SERVE_SEED = 2509
+SERVE_BUDGET = 150 << 30
+SERVE_CAPACITY_GPTS = 210.0   # measured 64-shot FP32 batch throughput
+SERVE_LOAD = 0.7
+
+
+def run_serve(n=2000, *, seed=SERVE_SEED, load=SERVE_LOAD, slots=64,
+              budget=SERVE_BUDGET, chunk=BATCH_CHUNK, device=0):
+    """Replay a Poisson stream of shot requests in real time through the
+    continuous-batching server; latency is arrival -> traces on the host.
+    The arrival rate is set so that the offered work is `load` times the
+    measured batched FP32 capacity."""
+    import torch
+    import workloads
+    from paper_2506_02486_gb300.runtime import Segment, Server
+    reqs = workloads.arrival_stream(seed, n=n, rate_per_s=1.0)
+    work = [r.nx * r.ny * r.nz * r.nsteps for r in reqs]
+    lam = load * SERVE_CAPACITY_GPTS * 1e9 / (sum(work) / len(work))
+    # same draws, rescaled inter-arrival times
+    arrivals = [r.arrival_s / lam for r in reqs]
+    profiles = {}
+    seg = Segment(budget + (8 << 30), device=device)
+    try:
+        srv = Server(seg, budget, max_slots=slots, chunk=chunk)
+        try:
+            tickets = []
+            t0 = time.perf_counter()
+            s0 = srv.now()
+            for r, a in zip(reqs, arrivals):
+                wait = a - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+                vz = workloads.layered_profile(r.nz, r.model_seed)
+                rec = workloads.lattice_receivers(r.nx, r.ny, r.sponge, n=8,
+                                                  margin=r.sponge)
+                tickets.append(srv.submit(
+                    r.nx, r.ny, r.nz, r.nsteps, src=r.source, f_peak=20.0,
+                    vz=vz, receivers=rec, dtype=r.dtype, sponge=r.sponge))
+            results = [srv.wait(t) for t in tickets]
+            st = srv.stats()
+        finally:
+            srv.close()
+    finally:
+        seg.close()
+    bad = [r["status"] for r in results if r["status"] != 0]
+    lat = np.array([r["done_s"] - r["submit_s"] for r in results])
+    qwait = np.array([r["admit_s"] - r["submit_s"] for r in results])
+    t_first = min(r["submit_s"] for r in results)
+    t_last = max(r["done_s"] for r in results)
+    pu = sum(r["points"] * r["steps"] for r in results)
+    by_dtype = {}
+    for q, r in zip(reqs, results):
+        by_dtype.setdefault(q.dtype, []).append(r["done_s"] - r["submit_s"])
+    return {
+        "requests": n, "seed": seed, "rate_per_s": lam, "offered_load": load,
+        "capacity_gpts_assumed": SERVE_CAPACITY_GPTS,
+        "budget_bytes": budget, "slots": slots, "chunk": chunk,
+        "failed": len(bad),
+        "p50_latency_s": float(np.percentile(lat, 50)),
+        "p99_latency_s": float(np.percentile(lat, 99)),
+        "mean_latency_s": float(lat.mean()),
+        "p99_queue_wait_s": float(np.percentile(qwait, 99)),
+        "latency_by_dtype_p50_s": {k: float(np.percentile(v, 50))
+                                   for k, v in by_dtype.items()},
+        "makespan_s": t_last - t_first,
+        "aggregate_gpts": pu / (t_last - t_first) / 1e9,
+        "busy_gpts": st["point_updates"] / max(st["busy_s"], 1e-9) / 1e9,
+        "point_updates": pu,
+        "max_active": st["max_active"], "chunks": st["chunks"],
+        "rebuilds": st["rebuilds"], "peak_bytes": st["peak_bytes"],
+    }
+
+
 def run_batch_modes(args):
     """The 64-shot workload under each schedule, one JSON line each."""
     import torch
@@ -585,15 +658,18 @@ def run_precision(args):
                 torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1)
                 u = s.u(f64=True)
+                tr = s.traces(steps).astype(np.float64)
                 info = s.info
         r = {"gpts": npts * steps / (ms * 1e-3) / 1e9, "ms": ms,
              "scale_u": info["scale_u"]}
         if ref is None:
-            ref = (u,)
+            ref = (u, tr)
         else:
             d = u - ref[0]
             r["rel_l2"] = float(np.linalg.norm(d) / np.linalg.norm(ref[0]))
             r["max_abs"] = float(np.abs(d).max())
+            r["traces_rel_l2"] = float(np.linalg.norm(tr - ref[1]) /
+                                       np.linalg.norm(ref[1]))
         res[dt] = r
         del u
     res["max_abs_u"] = float(np.abs(ref[0]).max())
@@ -618,11 +694,18 @@ def main():
     ap.add_argument("--dtype", default="f32", help="storage type for --case")
     ap.add_argument("--precision", action="store_true",
                     help="storage types vs FP64 on the 1024x1024x512 model")
+    ap.add_argument("--serve", type=int, default=0, metavar="N",
+                    help="replay N Poisson shot requests through the server")
     ap.add_argument("--batch", action="store_true",
                     help="64-shot batched workload: schedules compared")
     args = ap.parse_args()
     if args.batch:
         return run_batch_modes(args)
+    if args.serve:
+        from paper_2506_02486_gb300 import buildlib
+        buildlib.build()
+        print(json.dumps({"serving": run_serve(args.serve)}), flush=True)
+        return 0
     if args.case:
         return run_case(args)
     if args.precision:
