@@ -485,6 +485,12 @@ gw_status gw_domain_create(gw_ctx *c, const gw_shot_desc *desc, int px, int py,
     if (D.nx > 65535 || D.ny > 65535)
         return fail(GW_ERR_ARG, "nx, ny must be < 65536");
     if (D.dtype < DT_F32 || D.dtype > DT_BF16) return fail(GW_ERR_ARG, "bad dtype");
+    for (double sc : {D.scale_u, D.scale_w}) {
+        int e2 = 0;
+        // the kernels fold the scales into exact power-of-two factors
+        if (sc < 0 || (sc > 0 && (std::frexp(sc, &e2) != 0.5 || e2 < -30 || e2 > 30)))
+            return fail(GW_ERR_ARG, "scale %g is not a power of two in [2^-31, 2^29]", sc);
+    }
     if (px <= 0 || py <= 0 || pz <= 0) return fail(GW_ERR_ARG, "bad decomposition");
     int nsub = px * py * pz;
     if (nsub > c->nranks)

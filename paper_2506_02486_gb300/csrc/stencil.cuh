@@ -321,8 +321,13 @@ struct Step {
     int rank_;
     int nl_;                   // receivers + sources inside this item
     bool item_puts;            // fused puts: this tile touches a face with a neighbour
+    bool fast_;                // whole tile, no puts, sources or receivers
+    T *ust;                    // store address of this thread's first row at the compute plane
+    long long wdelta;          // w field minus u_{n+1} field (elements)
     size_t roff_[PY];          // in-plane element offset of each row's first point
-    M isu_, isw_, su_, sw_;
+    M isu_, q_, iq_;           // 1/su; q = sw/su and su/sw (delta storage)
+    // FP16 delta storage carries power-of-two scales; BF16 does not
+    static constexpr bool SCALED = DELTA && std::is_same<T, __half>::value;
     const double *gz_ptr;      // sponge factors along z of this subdomain
     M gz_next;                 // sponge factor of the next plane (prefetched)
     int cap_;
@@ -364,6 +369,9 @@ struct Step {
 
     __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity)
     {
+        // a completed phase needs no more than one probe; the bounded loop
+        // (and the abort bookkeeping) is the slow path
+        if (mbar_try_wait(bar, parity)) return true;
         if (aborted) return false;
         if (!wait_slot(bar, parity, abortf())) {
             if (!*abortf()) atomicOr(A.err, ERRB_TIMEOUT);
@@ -457,8 +465,9 @@ struct Step {
         rank_ = sd->rank;
 #pragma unroll
         for (int f = 0; f < 6; ++f) nbr_[f] = sd->nbr[f];
-        isu_ = (M)sh->isu; isw_ = (M)sh->isw;
-        su_ = (M)sh->su;   sw_ = (M)sh->sw;
+        isu_ = (M)sh->isu;
+        q_ = (M)(sh->sw * sh->isu);
+        iq_ = (M)(sh->su * sh->isw);
         cap_ = sh->cap;
         gz_ptr = sh->gz + sd->gz0;
         if (SPONGE) gz_next = (M)__ldg(gz_ptr + z0);
@@ -540,11 +549,15 @@ struct Step {
         }
         consumer_sync(C::NT);
         nl_ = misc()[0];
+        fast_ = x0 + TX <= nx && y0 + TY <= ny && !item_puts && nl_ == 0;
+        ust = unext + (size_t)(z0 + R) * plane_ + roff_[0];
+        wdelta = DELTA ? (long long)(wbuf - unext) : 0;
     }
 
     __device__ __forceinline__ void end_item(int it)
     {
         double v = (double)acc + (double)acc2.x + (double)acc2.y;
+        if (SCALED) v *= (double)isu_ * (double)isu_;   // sums of (su u)^2
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red()[tid >> 5] = v;
@@ -595,8 +608,6 @@ struct Step {
                 l = __ffma2_rn(c2, S[2], l);
                 l = __ffma2_rn(c3, S[3], l);
                 l = __ffma2_rn(c4, S[4], l);
-                // delta storage holds su * u: undo the power-of-two scale
-                if (DELTA) l = __fmul2_rn(l, make_float2(isu_, isu_));
                 if (h) out.b = l; else out.a = l;
             }
         } else {
@@ -611,7 +622,6 @@ struct Step {
                 l = fma_rn(W<M>::c2, s[2], l);
                 l = fma_rn(W<M>::c3, s[3], l);
                 l = fma_rn(W<M>::c4, s[4], l);
-                if (DELTA) l = mul_rn(l, isu_);
                 out.set(i, l);
             }
         }
@@ -619,6 +629,11 @@ struct Step {
 
     // 3-level: u' = G (2u - G u_prev + coef lap);
     // delta:   w' = G (w + coef lap),  u' = G u + w'.
+    // Delta storage holds U = su u and W = sw w with power-of-two scales, and
+    // the arithmetic runs on the stored values: lap(U) = su lap(u), so
+    // W' = G (W + (q coef) lap(U)) and U' = G U + W' / q with q = sw / su.
+    // Multiplying by a power of two is exact, so this gives the bits of the
+    // unscaled formulas scaled; BF16 storage is unscaled (q = 1).
     __device__ __forceinline__ void update_row(const G &u, const G &pa, const G &cf,
                                                const G &lap, const G &gxy, M gz,
                                                G &un, G &wn)
@@ -626,17 +641,17 @@ struct Step {
         if constexpr (PK) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const float2 U = u.pair(h), Pp = pa.pair(h), CF = cf.pair(h),
-                             L = lap.pair(h);
+                const float2 U = u.pair(h), Pp = pa.pair(h), L = lap.pair(h);
+                float2 CF = cf.pair(h);
                 float2 Gs = make_float2(1.0f, 1.0f);
                 if (SPONGE) Gs = __fmul2_rn(gxy.pair(h), make_float2(gz, gz));
                 float2 UN, WN = make_float2(0.0f, 0.0f);
                 if (DELTA) {
-                    const float2 w = __fmul2_rn(Pp, make_float2(isw_, isw_));
-                    const float2 uu = __fmul2_rn(U, make_float2(isu_, isu_));
-                    const float2 a = __ffma2_rn(CF, L, w);
+                    if (SCALED) CF = __fmul2_rn(CF, make_float2(q_, q_));
+                    const float2 a = __ffma2_rn(CF, L, Pp);
                     WN = SPONGE ? __fmul2_rn(Gs, a) : a;
-                    UN = SPONGE ? __ffma2_rn(Gs, uu, WN) : __fadd2_rn(uu, WN);
+                    const float2 wq = SCALED ? __fmul2_rn(WN, make_float2(iq_, iq_)) : WN;
+                    UN = SPONGE ? __ffma2_rn(Gs, U, wq) : __fadd2_rn(U, wq);
                 } else {
                     // 2u - G u_prev rounded once: fma(-G, u_prev, u + u)
                     const float2 nG = SPONGE ? make_float2(-Gs.x, -Gs.y)
@@ -652,12 +667,12 @@ struct Step {
             for (int i = 0; i < 4; ++i) {
                 M Gs = SPONGE ? mul_rn(gxy.get(i), gz) : M(1);
                 if (DELTA) {
-                    M w = mul_rn(pa.get(i), isw_);
-                    M uu = mul_rn(u.get(i), isu_);
-                    M a = fma_rn(cf.get(i), lap.get(i), w);
+                    M c = SCALED ? mul_rn(cf.get(i), q_) : cf.get(i);
+                    M a = fma_rn(c, lap.get(i), pa.get(i));
                     M wv = SPONGE ? mul_rn(Gs, a) : a;
+                    M wq = SCALED ? mul_rn(wv, iq_) : wv;
                     wn.set(i, wv);
-                    un.set(i, SPONGE ? fma_rn(Gs, uu, wv) : add_rn(uu, wv));
+                    un.set(i, SPONGE ? fma_rn(Gs, u.get(i), wq) : add_rn(u.get(i), wq));
                 } else {
                     M tt = fma_rn(-Gs, pa.get(i), add_rn(u.get(i), u.get(i)));
                     M a = fma_rn(cf.get(i), lap.get(i), tt);
@@ -683,134 +698,175 @@ struct Step {
             if (i < vx) acc = fma_rn(un.get(i), un.get(i), acc);
     }
 
-    // ---- one u-plane iteration -----------------------------------------
+    // ---- the z loop of one item --------------------------------------
     // Queue entries 0..7 hold this thread's points on the 8 planes before the
-    // one that arrives now, which lands in entry 8 + P (P = phase within the
-    // trip); the compute plane is the one 4 back.  The trip loop shifts the
-    // queue by KP planes after its KP phases.
-    template <int P>
-    __device__ __forceinline__ void iter(int t)
+    // one that arrives; the arriving plane lands in entry 8 + P (P = phase
+    // within a trip of KP planes) and the compute plane is the one 4 back.
+
+    // Fill: the item's first 8 planes (interior z0 - 4 .. z0 + 3) only enter
+    // the queue.  Each plane load is handed back 4 loads later.
+    template <int QI>
+    __device__ __forceinline__ void fill_one()
     {
-        // (1) the plane of load t: append its centre values to the queue
+        unsigned slot = tg % SU;
+        wait_or_abort(ufull(slot), (tg / SU) & 1u);
+        const T *pl = ubuf(slot);
+#pragma unroll
+        for (int r = 0; r < PY; ++r)
+            ld_grp<T, PK>(pl + (PY * ty + r + R) * C::RW + HL + 4 * tx, Q[QI][r]);
+        __syncwarp();
+        if (lane == 0 && tg >= R) mbar_arrive(uempty((tg - R) % SU));
+        ++tg;
+    }
+
+    // One compute plane z.  FAST: a whole tile (every row and point valid)
+    // with no halo puts, sources or receivers.
+    template <int P, bool FAST>
+    __device__ __forceinline__ void step_plane(int z)
+    {
+        // (1) x/y neighbours from the compute plane, staged R loads ago (its
+        // full barrier was waited on then): issued before the waits below
+        const T *pl = ubuf((tg - R) % SU);
+        G yv[PY + 8], lf[PY], rt[PY];
+#pragma unroll
+        for (int j = 0; j < PY + 8; ++j)
+            ld_grp<T, PK>(pl + (PY * ty + j) * C::RW + HL + 4 * tx, yv[j]);
+#pragma unroll
+        for (int r = 0; r < PY; ++r) {
+            const T *row = pl + (PY * ty + r + R) * C::RW + HL + 4 * tx;
+            ld_grp<T, PK>(row - 4, lf[r]);
+            ld_grp<T, PK>(row + 4, rt[r]);
+        }
+        // (2) the plane that arrives now: the z + 4 neighbours
         {
             unsigned slot = tg % SU;
             wait_or_abort(ufull(slot), (tg / SU) & 1u);
-            const T *pl = ubuf(slot);
+            const T *pn = ubuf(slot);
 #pragma unroll
             for (int r = 0; r < PY; ++r)
-                ld_grp<T, PK>(pl + (PY * ty + r + R) * C::RW + HL + 4 * tx, Q[8 + P][r]);
+                ld_grp<T, PK>(pn + (PY * ty + r + R) * C::RW + HL + 4 * tx, Q[8 + P][r]);
         }
-        // (2) compute plane z = z0 + t - 8 once the queue is full
-        if (t >= 2 * R) {
-            const int z = z0 + t - 2 * R;
-            const T *pl = ubuf((tg - R) % SU);
-            unsigned ps = jg % SP;
-            wait_or_abort(pfull(ps), (jg / SP) & 1u);
-            G yv[PY + 8];
+        // (3) the pointwise tiles of plane z
+        unsigned ps = jg % SP;
+        wait_or_abort(pfull(ps), (jg / SP) & 1u);
+        G pa[PY], cf[PY];
 #pragma unroll
-            for (int j = 0; j < PY + 8; ++j)
-                ld_grp<T, PK>(pl + (PY * ty + j) * C::RW + HL + 4 * tx, yv[j]);
-            G lf[PY], rt[PY], pa[PY], cf[PY];
+        for (int r = 0; r < PY; ++r) {
+            ld_grp<T, PK>(pbuf(ps, 0) + (PY * ty + r) * TX + 4 * tx, pa[r]);
+            ld_grp<typename C::CT, PK>(
+                reinterpret_cast<const typename C::CT *>(pbuf(ps, 1)) +
+                    (PY * ty + r) * TX + 4 * tx, cf[r]);
+        }
+        M gz = M(1);
+        if (SPONGE) {
+            gz = gz_next;                       // loaded one plane ago
+            if (z + 1 < z1) gz_next = (M)__ldg(gz_ptr + z + 1);
+        }
+        G lap[PY];
 #pragma unroll
-            for (int r = 0; r < PY; ++r) {
-                const T *row = pl + (PY * ty + r + R) * C::RW + HL + 4 * tx;
-                ld_grp<T, PK>(row - 4, lf[r]);
-                ld_grp<T, PK>(row + 4, rt[r]);
-                ld_grp<T, PK>(pbuf(ps, 0) + (PY * ty + r) * TX + 4 * tx, pa[r]);
-                ld_grp<typename C::CT, PK>(
-                    reinterpret_cast<const typename C::CT *>(pbuf(ps, 1)) +
-                        (PY * ty + r) * TX + 4 * tx, cf[r]);
+        for (int r = 0; r < PY; ++r) laplacian_row<P>(yv, lf[r], rt[r], r, lap[r]);
+        if (!FAST) add_sources(z, lap);
+        // leapfrog update with the sponge
+        G un[PY], wn[PY];
+#pragma unroll
+        for (int r = 0; r < PY; ++r)
+            update_row(yv[r + R], pa[r], cf[r], lap[r], gxy[r], gz, un[r], wn[r]);
+        // stores: u' (and w') at this plane; norm partial
+#pragma unroll
+        for (int r = 0; r < PY; ++r) {
+            T *up = ust + r * (long long)px_;
+            M so[4], sw[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                so[i] = un[r].get(i);
+                sw[i] = wn[r].get(i);
             }
-            M gz = M(1);
-            if (SPONGE) {
-                gz = gz_next;                       // loaded one plane ago
-                if (z + 1 < z1) gz_next = (M)__ldg(gz_ptr + z + 1);
-            }
-            const int nl = nl_;
-            G lap[PY];
-#pragma unroll
-            for (int r = 0; r < PY; ++r) laplacian_row<P>(yv, lf[r], rt[r], r, lap[r]);
-            // point sources: lap += wavelet[n] at the source cell (the loop
-            // only finds the point; the add is a select over compile-time
-            // indices, so lap stays in registers)
-            if (nl) {
-                for (int e = 0; e < nl; ++e) {
-                    int4 q = loc()[e];
-                    if (q.x < 0 && q.z == z) {
-                        int lx = q.y & 0xffff, ly = q.y >> 16;
-                        if ((lx >> 2) == tx && ly / PY == ty && n < cap_) {
-                            const int k = (ly % PY) * 4 + (lx & 3);
-                            const M wv = (M)__ldg(sh->wavelet + (size_t)(-1 - q.x) * cap_ + n);
-#pragma unroll
-                            for (int r = 0; r < PY; ++r)
-#pragma unroll
-                                for (int i = 0; i < 4; ++i)
-                                    lap[r].set(i, (k == r * 4 + i) ? add_rn(lap[r].get(i), wv) : lap[r].get(i));
-                        }
-                    }
-                }
-            }
-            // leapfrog update with the sponge
-            G un[PY], wn[PY];
-#pragma unroll
-            for (int r = 0; r < PY; ++r)
-                update_row(yv[r + R], pa[r], cf[r], lap[r], gxy[r], gz, un[r], wn[r]);
-            // stores: u' (and w') at this plane; norm partial
-            const size_t zoff = (size_t)(z + R) * plane_;
-#pragma unroll
-            for (int r = 0; r < PY; ++r) {
-                if (!rowok[r] || vx == 0) continue;
-                const size_t off = zoff + roff_[r];
-                M so[4], sw[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    so[i] = DELTA ? mul_rn(un[r].get(i), su_) : un[r].get(i);
-                    sw[i] = DELTA ? mul_rn(wn[r].get(i), sw_) : M(0);
-                }
-                accumulate_norm(un[r]);
-                if (vx == 4) {
-                    S::st4(unext + off, so);
-                    if (DELTA) S::st4(wbuf + off, sw);
+            if (FAST) {
+                if constexpr (PK) {
+                    acc2 = __ffma2_rn(un[r].a, un[r].a, acc2);
+                    acc2 = __ffma2_rn(un[r].b, un[r].b, acc2);
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        if (i < vx) {
-                            S::st1(unext + off + i, so[i]);
-                            if (DELTA) S::st1(wbuf + off + i, sw[i]);
-                        }
-                    }
+                    for (int i = 0; i < 4; ++i) acc = fma_rn(so[i], so[i], acc);
                 }
-                if (item_puts) put_halo_row(x0 + 4 * tx, y0 + PY * ty + r, z, so);
+                S::st4(up, so);
+                if (DELTA) S::st4(up + wdelta, sw);
+                continue;
             }
-            // receivers: trace[n] = u_{n+1}
-            if (nl) {
-                for (int e = 0; e < nl; ++e) {
-                    int4 q = loc()[e];
-                    if (q.x >= 0 && q.z == z) {
-                        int lx = q.y & 0xffff, ly = q.y >> 16;
-                        if ((lx >> 2) == tx && ly / PY == ty && n < cap_) {
-                            const int k = (ly % PY) * 4 + (lx & 3);
-                            M v = M(0);
+            if (!rowok[r] || vx == 0) continue;
+            accumulate_norm(un[r]);
+            if (vx == 4) {
+                S::st4(up, so);
+                if (DELTA) S::st4(up + wdelta, sw);
+            } else {
 #pragma unroll
-                            for (int r = 0; r < PY; ++r)
-#pragma unroll
-                                for (int i = 0; i < 4; ++i)
-                                    v = (k == r * 4 + i) ? un[r].get(i) : v;
-                            sh->traces[(size_t)q.x * cap_ + n] = (float)v;
-                        }
+                for (int i = 0; i < 4; ++i) {
+                    if (i < vx) {
+                        S::st1(up + i, so[i]);
+                        if (DELTA) S::st1(up + wdelta + i, sw[i]);
                     }
                 }
             }
+            if (item_puts) put_halo_row(x0 + 4 * tx, y0 + PY * ty + r, z, so);
         }
-        // (3) hand slots back: load tg - 4 (its last use, as the x/y plane,
-        // was this iteration) and the pointwise tile just used
+        if (!FAST) record_receivers(z, un);
+        ust += plane_;
+        // (4) hand slots back: the compute plane's load (its last use) and
+        // the pointwise tiles
         __syncwarp();
         if (lane == 0) {
-            if (tg >= R) mbar_arrive(uempty((tg - R) % SU));
-            if (t >= 2 * R) mbar_arrive(pempty(jg % SP));
+            mbar_arrive(uempty((tg - R) % SU));
+            mbar_arrive(pempty(ps));
         }
-        if (t >= 2 * R) ++jg;
+        ++jg;
         ++tg;
+    }
+
+    // point sources: lap += wavelet[n] at the source cell, in the stored
+    // scale (the loop only finds the point; the add is a select over
+    // compile-time indices, so lap stays in registers)
+    __device__ __forceinline__ void add_sources(int z, G (&lap)[PY])
+    {
+        const int nl = nl_;
+        for (int e = 0; e < nl; ++e) {
+            int4 q = loc()[e];
+            if (q.x < 0 && q.z == z) {
+                int lx = q.y & 0xffff, ly = q.y >> 16;
+                if ((lx >> 2) == tx && ly / PY == ty && n < cap_) {
+                    const int k = (ly % PY) * 4 + (lx & 3);
+                    M wv = (M)__ldg(sh->wavelet + (size_t)(-1 - q.x) * cap_ + n);
+                    if (SCALED) wv = mul_rn(wv, (M)sh->su);
+#pragma unroll
+                    for (int r = 0; r < PY; ++r)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            lap[r].set(i, (k == r * 4 + i) ? add_rn(lap[r].get(i), wv) : lap[r].get(i));
+                }
+            }
+        }
+    }
+
+    // receivers: trace[n] = u_{n+1} (unscaled)
+    __device__ __forceinline__ void record_receivers(int z, const G (&un)[PY])
+    {
+        const int nl = nl_;
+        for (int e = 0; e < nl; ++e) {
+            int4 q = loc()[e];
+            if (q.x >= 0 && q.z == z) {
+                int lx = q.y & 0xffff, ly = q.y >> 16;
+                if ((lx >> 2) == tx && ly / PY == ty && n < cap_) {
+                    const int k = (ly % PY) * 4 + (lx & 3);
+                    M v = M(0);
+#pragma unroll
+                    for (int r = 0; r < PY; ++r)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            v = (k == r * 4 + i) ? un[r].get(i) : v;
+                    if (SCALED) v = mul_rn(v, isu_);
+                    sh->traces[(size_t)q.x * cap_ + n] = (float)v;
+                }
+            }
+        }
     }
 
     __device__ __forceinline__ void shift_queue()
@@ -819,6 +875,22 @@ struct Step {
         for (int q = 0; q < 8; ++q)
 #pragma unroll
             for (int r = 0; r < PY; ++r) Q[q][r] = Q[q + KP][r];
+    }
+
+    // the compute planes of one item, KP per trip of the loop
+    template <bool FAST>
+    __device__ __forceinline__ void z_loop(int nzc)
+    {
+#pragma unroll 1
+        for (int tb = 0; tb < nzc; tb += KP) {
+            step_plane<0, FAST>(z0 + tb);
+            if (tb + 1 < nzc) step_plane<1, FAST>(z0 + tb + 1);
+            if constexpr (KP > 2) {
+                if (tb + 2 < nzc) step_plane<2, FAST>(z0 + tb + 2);
+                if (tb + 3 < nzc) step_plane<3, FAST>(z0 + tb + 3);
+            }
+            shift_queue();
+        }
     }
 
     // One-sided puts of a freshly computed row segment into the halos of
@@ -896,14 +968,10 @@ struct Step {
             kk = A.k + k;
             for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
                 begin_item(it);
-                const int T = z1 - z0 + 2 * R;
-                static_assert(KP == 2, "the trip loop below runs two phases");
-#pragma unroll 1
-                for (int tb = 0; tb < T; tb += KP) {
-                    iter<0>(tb);
-                    if (tb + 1 < T) iter<1>(tb + 1);
-                    shift_queue();
-                }
+                fill_one<0>(); fill_one<1>(); fill_one<2>(); fill_one<3>();
+                fill_one<4>(); fill_one<5>(); fill_one<6>(); fill_one<7>();
+                if (fast_) z_loop<true>(z1 - z0);
+                else z_loop<false>(z1 - z0);
                 end_item(it);
             }
             if (k + 1 < A.nk) {
