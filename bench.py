@@ -613,7 +613,7 @@ def run_case(args):
     shot = workloads.layered_cube(n)
     with Segment(4 * padded_bytes(n, n, n, args.dtype) + (512 << 20)) as seg:
         with Shot(seg, n, n, n, nsteps=args.steps, sponge=shot.sponge,
-                  dtype=args.dtype, chunk=-1) as s:
+                  dtype=args.dtype, chunk=-1, tile=args.tile) as s:
             s.set_model(shot.vel)
             s.add_ricker(shot.src, shot.f_peak)
             s.set_receivers(shot.receivers)
@@ -692,6 +692,7 @@ def main():
     ap.add_argument("--case", type=int, default=0,
                     help="run one plain N^3 shot for --steps steps (profiling)")
     ap.add_argument("--dtype", default="f32", help="storage type for --case")
+    ap.add_argument("--tile", type=int, default=0, help="kernel tile for --case")
     ap.add_argument("--precision", action="store_true",
                     help="storage types vs FP64 on the 1024x1024x512 model")
     ap.add_argument("--serve", type=int, default=0, metavar="N",

@@ -11,7 +11,7 @@
 namespace gw {
 
 // Cfg<storage, tile x, tile y, rows per thread, u-ring slots, pointwise
-//     slots, CTAs per SM wanted, packed f32x2 math>
+//     slots, CTAs per SM wanted, packed f32x2 math, planes per queue shift>
 #if GW_INST == 0
 using C = Cfg<float, 64, 28, 2, 8, 4>;  constexpr bool kDelta = false;
 #elif GW_INST == 1
