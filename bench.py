@@ -359,7 +359,7 @@ def run_batch(dtype="f32", *, seed=BATCH_SEED, steps=BATCH_STEPS,
         if autotune:
             descs = [gw.shot_desc(b.side, b.side, b.side, nsteps=steps,
                                   dtype=dtype, sponge=b.sponge) for b in plan]
-            for b, t in zip(plan, gw.gw_plan_tiles(seg.ctx, descs, 20)):
+            for b, t in zip(plan, gw.gw_plan_tiles(seg.ctx, descs, 20, 0.1)):
                 tiles[b.side] = t
         out["autotune_s"] = time.perf_counter() - t0
         out["tiles"] = {str(k): v for k, v in tiles.items()}

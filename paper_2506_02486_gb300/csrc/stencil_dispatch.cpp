@@ -21,11 +21,13 @@ struct Entry {
     TileInfo (*info)();
 };
 #define GW_E(I, D, ID) {D, ID, step_launch_##I, step_occ_##I, step_info_##I}
+// id 0 of each storage type is its default tile: the fastest on the 512^3
+// layered shot (FP32 64x28 with a 10-slot ring, 16-bit 128x14).
 const Entry kTable[] = {
-    GW_E(0, DT_F32, 0),  GW_E(1, DT_F32, 1),   GW_E(2, DT_F32, 2),
-    GW_E(3, DT_F32, 3),  GW_E(4, DT_F64, 0),   GW_E(5, DT_F64, 1),
-    GW_E(6, DT_F16S, 0), GW_E(7, DT_F16S, 1),  GW_E(8, DT_F16S, 2),
-    GW_E(9, DT_BF16, 0), GW_E(10, DT_BF16, 1), GW_E(11, DT_BF16, 2),
+    GW_E(3, DT_F32, 0),  GW_E(1, DT_F32, 1),   GW_E(2, DT_F32, 2),
+    GW_E(0, DT_F32, 3),  GW_E(4, DT_F64, 0),   GW_E(5, DT_F64, 1),
+    GW_E(7, DT_F16S, 0), GW_E(6, DT_F16S, 1),  GW_E(8, DT_F16S, 2),
+    GW_E(10, DT_BF16, 0), GW_E(9, DT_BF16, 1), GW_E(11, DT_BF16, 2),
     GW_E(12, DT_F32, 4), GW_E(13, DT_F32, 5),  GW_E(14, DT_F32, 6),
     GW_E(15, DT_F16S, 3),
 };

@@ -50,7 +50,7 @@ def test_plain_64cubed_matches_oracle():
     assert g["norms"] == pytest.approx(o["norms"], rel=TOL32)
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3, 4])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7])
 def test_ragged_layered_sponge_matches_oracle(tile):
     """Non-multiple sizes in every axis (ragged tiles and x tails), a
     layered model, a 6-cell sponge, an off-centre source, every FP32 tile."""
@@ -75,6 +75,24 @@ def test_tiles_and_graphs_do_not_change_bits():
                             (1, 25, 33)]]
     for r in runs[1:]:
         assert np.array_equal(r["u32"], runs[0]["u32"])
+
+
+@pytest.mark.parametrize("dtype,tiles", [("f16s", [1, 2, 3, 4]),
+                                         ("bf16", [1, 2, 3])])
+def test_delta_tiles_do_not_change_bits(dtype, tiles):
+    """16-bit delta storage: every tile, z-chunking and launch mode gives
+    the same bits (the stored values and the traces)."""
+    nx, ny, nz = 70, 45, 33
+    vel = workloads.layered(nx, ny, nz, seed=3)
+    rec = workloads.lattice_receivers(nx, ny, 5, n=3, margin=5)
+    runs = [gpu_run(vel, 37, src=(30, 20, 16), f_peak=25.0, sponge=5,
+                    receivers=rec, dtype=dtype, tile=t, chunk=c, zchunk=z)
+            for t, c, z in [(tiles[0], 0, 0)] +
+            [(t, 7, 5 + 4 * i) for i, t in enumerate(tiles[1:])] +
+            [(tiles[0], -1, 33)]]
+    for r in runs[1:]:
+        assert np.array_equal(r["u32"], runs[0]["u32"])
+        assert np.array_equal(r["traces"], runs[0]["traces"])
 
 
 @pytest.mark.parametrize("shape", [(8, 8, 8), (9, 5, 3), (1, 1, 1),
