@@ -2,6 +2,8 @@
 // (vmax, coef = (v dt / h)^2 in FP64), dense <-> padded field transfers,
 // the separate face-halo put (pack/put/unpack of Listing 1, section 4.5),
 // the end-of-chunk FP64 norm reduction, and the FP64 energy check.
+#include <algorithm>
+#include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -195,46 +197,60 @@ __device__ __forceinline__ void face_box(const SubDev &s, const SubDev &d,
     }
 }
 
+// One grid row (blockIdx.y) per face copy; its threads stride over the
+// 16-byte units (V elements along x) of that face's box.  A unit whose source
+// and destination are both 16-byte aligned moves as one vector; a short or
+// misaligned one element by element.
 template <class E>
-__global__ void k_halo(const HaloDesc *descs, int ndesc, long long total,
-                       const SubDev *subs, const int *step, int k, int xo)
+__global__ void k_halo(const HaloDesc *descs, const SubDev *subs, const int *step,
+                       int k, int xo)
 {
-    int buf = (*step + k + 1) & 1;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-         i < total; i += (long long)gridDim.x * blockDim.x) {
-        int di = 0;
-        while (di + 1 < ndesc && descs[di + 1].first <= i) ++di;
-        const HaloDesc hd = descs[di];
-        const SubDev &s = subs[hd.src];
-        const SubDev &d = subs[hd.dst];
-        int ex, ey, ez, sx, sy, sz, dx, dy, dz;
-        face_box(s, d, hd.face, ex, ey, ez, sx, sy, sz, dx, dy, dz);
-        long long j = i - hd.first;
-        int a = (int)(j % ex);
-        int b = (int)((j / ex) % ey);
-        int c = (int)(j / ((long long)ex * ey));
+    constexpr int V = 16 / (int)sizeof(E);
+    const HaloDesc hd = descs[blockIdx.y];
+    const SubDev &s = subs[hd.src];
+    const SubDev &d = subs[hd.dst];
+    int ex, ey, ez, sx, sy, sz, dx, dy, dz;
+    face_box(s, d, hd.face, ex, ey, ez, sx, sy, sz, dx, dy, dz);
+    const int buf = (*step + k + 1) & 1;
+    const E *src = reinterpret_cast<const E *>(s.u[buf]);
+    E *dst = reinterpret_cast<E *>(d.u[buf]);
+    const unsigned ux = (unsigned)(ex + V - 1) / V;
+    const unsigned units = ux * (unsigned)ey * (unsigned)ez;
+    const int fx = hd.face >> 1;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < units;
+         i += gridDim.x * blockDim.x) {
+        const unsigned row = i / ux;
+        const int a = (int)(i - row * ux) * V;
+        const int b = (int)(row % (unsigned)ey);
+        const int c = (int)(row / (unsigned)ey);
         // the halo cell of d keeps d's own x/y/z for the axes not crossed
-        const E *src = reinterpret_cast<const E *>(s.u[buf]);
-        E *dst = reinterpret_cast<E *>(d.u[buf]);
-        int fx = hd.face >> 1;
-        int tx = fx == 0 ? dx + a : a;
-        int ty = fx == 1 ? dy + b : b;
-        int tz = fx == 2 ? dz + c : c;
-        dst[pidx(d, xo, tx, ty, tz)] = src[pidx(s, xo, sx + a, sy + b, sz + c)];
+        const int tx = fx == 0 ? dx + a : a;
+        const int ty = fx == 1 ? dy + b : b;
+        const int tz = fx == 2 ? dz + c : c;
+        const E *ps = src + pidx(s, xo, sx + a, sy + b, sz + c);
+        E *pd = dst + pidx(d, xo, tx, ty, tz);
+        const int n = min(V, ex - a);
+        if (n == V && ((reinterpret_cast<uintptr_t>(ps) | reinterpret_cast<uintptr_t>(pd)) & 15u) == 0) {
+            *reinterpret_cast<uint4 *>(pd) = *reinterpret_cast<const uint4 *>(ps);
+        } else {
+            for (int q = 0; q < n; ++q) pd[q] = ps[q];
+        }
     }
 }
 
-cudaError_t launch_halo(const HaloDesc *descs, int ndesc, long long total,
+cudaError_t launch_halo(const HaloDesc *descs, int ndesc, long long max_units,
                         const SubDev *subs_dev, const int *step, int k,
                         int dtype, cudaStream_t s)
 {
-    if (total <= 0 || ndesc <= 0) return cudaSuccess;
-    int g = grid_for((size_t)total);
-    int xo = dtype_xoff(dtype);
+    if (max_units <= 0 || ndesc <= 0) return cudaSuccess;
+    if (ndesc > 65535 || max_units > 0xffffffffLL) return cudaErrorInvalidValue;
+    const int gx = (int)std::min<long long>((max_units + 255) / 256, 1024);
+    const dim3 grid(gx, ndesc);
+    const int xo = dtype_xoff(dtype);
     switch (dtype_size(dtype)) {
-    case 2: k_halo<unsigned short><<<g, 256, 0, s>>>(descs, ndesc, total, subs_dev, step, k, xo); break;
-    case 4: k_halo<unsigned int><<<g, 256, 0, s>>>(descs, ndesc, total, subs_dev, step, k, xo); break;
-    default: k_halo<unsigned long long><<<g, 256, 0, s>>>(descs, ndesc, total, subs_dev, step, k, xo); break;
+    case 2: k_halo<unsigned short><<<grid, 256, 0, s>>>(descs, subs_dev, step, k, xo); break;
+    case 4: k_halo<unsigned int><<<grid, 256, 0, s>>>(descs, subs_dev, step, k, xo); break;
+    default: k_halo<unsigned long long><<<grid, 256, 0, s>>>(descs, subs_dev, step, k, xo); break;
     }
     return cudaGetLastError();
 }

@@ -146,21 +146,23 @@ void build_items(gw_domain *d)
 void build_halo_plan(gw_domain *d)
 {
     d->halo.clear();
-    long long tot = 0;
+    // the copy kernel moves rows in 16-byte units of V elements
+    const long long V = 16 / d->esize();
+    long long most = 0;
     for (int si = 0; si < d->nsub(); ++si) {
         const SubDev &s = d->subs[si];
         for (int f = 0; f < 6; ++f) {
             int nb = s.nbr[f];
             if (nb < 0) continue;
-            long long cnt = (f >> 1) == 0 ? (long long)R * s.ny * s.nz
-                          : (f >> 1) == 1 ? (long long)s.nx * R * s.nz
-                                          : (long long)s.nx * s.ny * R;
-            HaloDesc h{si, nb, f, 0, tot};
+            long long units = (f >> 1) == 0 ? (R + V - 1) / V * s.ny * s.nz
+                            : (f >> 1) == 1 ? (s.nx + V - 1) / V * R * s.nz
+                                            : (s.nx + V - 1) / V * s.ny * R;
+            HaloDesc h{si, nb, f, 0, 0};
             d->halo.push_back(h);
-            tot += cnt;
+            most = std::max(most, units);
         }
     }
-    d->halo_total = tot;
+    d->halo_units = most;
 }
 
 gw_status plan_schedule(gw_domain *d)
@@ -313,7 +315,7 @@ gw_status enqueue_chunk(gw_domain *d, int nk, cudaStream_t s, bool timed)
                 h1 = pool_event(d);
                 GW_TRY_CUDA(cudaEventRecord(h0, s));
             }
-            GW_TRY_CUDA(launch_halo(d->d_halo, (int)d->halo.size(), d->halo_total,
+            GW_TRY_CUDA(launch_halo(d->d_halo, (int)d->halo.size(), d->halo_units,
                                     d->d_subs, d->d_step, k, d->dtype, s));
             if (timed) {
                 GW_TRY_CUDA(cudaEventRecord(h1, s));
@@ -974,7 +976,7 @@ gw_status gw_put_halo(gw_domain *d, gw_stream stream)
     if (d->halo.empty()) return GW_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     d->last = s;
-    GW_TRY_CUDA(launch_halo(d->d_halo, (int)d->halo.size(), d->halo_total, d->d_subs,
+    GW_TRY_CUDA(launch_halo(d->d_halo, (int)d->halo.size(), d->halo_units, d->d_subs,
                             d->d_step, -1, d->dtype, s));
     return GW_OK;
 }
@@ -1081,7 +1083,7 @@ gw_status gw_write_wavefield(gw_domain *d, int which, const void *in, int f64)
     }
     // refresh the face halos of the written field
     if (!d->halo.empty() && (f == 0 || f == 1))
-        GW_TRY_CUDA(launch_halo(d->d_halo, (int)d->halo.size(), d->halo_total, d->d_subs,
+        GW_TRY_CUDA(launch_halo(d->d_halo, (int)d->halo.size(), d->halo_units, d->d_subs,
                                 d->d_step, f == 0 ? -1 : -2, d->dtype, nullptr));
     GW_TRY_CUDA(cudaDeviceSynchronize());
     return GW_OK;

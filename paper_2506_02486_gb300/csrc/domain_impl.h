@@ -62,7 +62,7 @@ struct gw_domain {
     int grid = 0, nitems = 0, chunk = gw::kDefaultChunk, zc = 0;
     std::vector<Item> items;
     std::vector<HaloDesc> halo;
-    long long halo_total = 0;
+    long long halo_units = 0;
     // sources and receivers (host copies)
     std::vector<int4> srcs;
     std::vector<std::vector<double>> wavelets;

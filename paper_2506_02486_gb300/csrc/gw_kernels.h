@@ -75,11 +75,12 @@ struct HaloDesc {
     int pad_;
     long long first;   // prefix offset of this descriptor's elements
 };
-// Copy all face halos for descriptors [0, ndesc); total = number of
-// elements over all descriptors.  The buffer refreshed is
-// u[(*step + k + 1) & 1]: the new field after step k of the current chunk,
-// or (k = -1) the current field u_n.
-cudaError_t launch_halo(const HaloDesc *descs, int ndesc, long long total,
+// Copy all face halos for descriptors [0, ndesc); max_units = the largest
+// number of 16-byte units (rows cut into pieces of 16 / element-size
+// elements) of any one face.  The buffer refreshed is u[(*step + k + 1) & 1]:
+// the new field after step k of the current chunk, or (k = -1) the current
+// field u_n.
+cudaError_t launch_halo(const HaloDesc *descs, int ndesc, long long max_units,
                         const SubDev *subs_dev, const int *step, int k,
                         int dtype, cudaStream_t s);
 

@@ -322,7 +322,8 @@ struct Step {
     int rank_;
     int nl_;                   // receivers + sources inside this item
     bool item_puts;            // fused puts: this tile touches a face with a neighbour
-    bool fast_;                // whole tile, no puts, sources or receivers
+    bool fast_;                // whole tile, no sources or receivers
+    bool tput_;                // fused puts: this thread's points touch an x or y face
     T *ust;                    // store address of this thread's first row at the compute plane
     long long wdelta;          // w field minus u_{n+1} field (elements)
     size_t roff_[PY];          // in-plane element offset of each row's first point
@@ -554,7 +555,13 @@ struct Step {
         }
         consumer_sync(C::NT);
         nl_ = misc()[0];
-        fast_ = x0 + TX <= nx && y0 + TY <= ny && !item_puts && nl_ == 0;
+        fast_ = x0 + TX <= nx && y0 + TY <= ny && nl_ == 0;
+        {
+            const int xs = x0 + 4 * tx, ys = y0 + PY * ty;
+            tput_ = item_puts &&
+                    ((xs < R && nbr_[0] >= 0) || (xs + 4 > nx - R && nbr_[1] >= 0) ||
+                     (ys < R && nbr_[2] >= 0) || (ys + PY > ny - R && nbr_[3] >= 0));
+        }
         ust = unext + (size_t)(z0 + R) * plane_ + roff_[0];
         wdelta = DELTA ? (long long)(wbuf - unext) : 0;
     }
@@ -726,7 +733,7 @@ struct Step {
 
     // One compute plane z.  FAST: a whole tile (every row and point valid)
     // with no halo puts, sources or receivers.
-    template <int P, bool FAST>
+    template <int P, bool FAST, bool PUTS>
     __device__ __forceinline__ void step_plane(int z)
     {
         // (1) x/y neighbours from the compute plane, staged R loads ago (its
@@ -777,6 +784,7 @@ struct Step {
         for (int r = 0; r < PY; ++r)
             update_row(yv[r + R], pa[r], cf[r], lap[r], gxy[r], gz, un[r], wn[r]);
         // stores: u' (and w') at this plane; norm partial
+        const bool zput = PUTS && ((z < R && nbr_[4] >= 0) || (z >= nz - R && nbr_[5] >= 0));
 #pragma unroll
         for (int r = 0; r < PY; ++r) {
             T *up = ust + r * (long long)px_;
@@ -796,6 +804,7 @@ struct Step {
                 }
                 S::st4(up, so);
                 if (DELTA) S::st4(up + wdelta, sw);
+                if (PUTS && (tput_ || zput)) put_halo_row(x0 + 4 * tx, y0 + PY * ty + r, z, so);
                 continue;
             }
             if (!rowok[r] || vx == 0) continue;
@@ -883,16 +892,16 @@ struct Step {
     }
 
     // the compute planes of one item, KP per trip of the loop
-    template <bool FAST>
+    template <bool FAST, bool PUTS>
     __device__ __forceinline__ void z_loop(int nzc)
     {
 #pragma unroll 1
         for (int tb = 0; tb < nzc; tb += KP) {
-            step_plane<0, FAST>(z0 + tb);
-            if (tb + 1 < nzc) step_plane<1, FAST>(z0 + tb + 1);
+            step_plane<0, FAST, PUTS>(z0 + tb);
+            if (tb + 1 < nzc) step_plane<1, FAST, PUTS>(z0 + tb + 1);
             if constexpr (KP > 2) {
-                if (tb + 2 < nzc) step_plane<2, FAST>(z0 + tb + 2);
-                if (tb + 3 < nzc) step_plane<3, FAST>(z0 + tb + 3);
+                if (tb + 2 < nzc) step_plane<2, FAST, PUTS>(z0 + tb + 2);
+                if (tb + 3 < nzc) step_plane<3, FAST, PUTS>(z0 + tb + 3);
             }
             shift_queue();
         }
@@ -975,8 +984,9 @@ struct Step {
                 begin_item(it);
                 fill_one<0>(); fill_one<1>(); fill_one<2>(); fill_one<3>();
                 fill_one<4>(); fill_one<5>(); fill_one<6>(); fill_one<7>();
-                if (fast_) z_loop<true>(z1 - z0);
-                else z_loop<false>(z1 - z0);
+                if (fast_ && !item_puts) z_loop<true, false>(z1 - z0);
+                else if (fast_) z_loop<true, true>(z1 - z0);
+                else z_loop<false, true>(z1 - z0);
                 end_item(it);
             }
             if (k + 1 < A.nk) {
