@@ -421,14 +421,15 @@ int make_items(const std::vector<SubDev> &subs, const TileInfo &ti, int grid,
     }
     int zc = zchunk;
     if (zc <= 0) {
-        // Items of 16 to 72 planes (measured on 512^3: 52-86-plane items
-        // run fastest, 64 best for FP32; 128 planes 3 % and one item per
-        // CTA 17 % slower), chosen to fill the last round of `grid` CTAs:
-        // cost = rounds * (planes + 8 * alpha), where a streamed-only halo
-        // plane costs alpha = 0.5 of a computed one.
+        // Items of 16 to ti.zcap planes (measured on 512^3: 52-86-plane
+        // items run fastest, 64 best for FP32; 128 planes 3 % and one item
+        // per CTA 17 % slower), chosen to fill the last round of `grid`
+        // CTAs: cost = rounds * (planes + 8 * alpha), where a streamed-only
+        // halo plane costs alpha = 0.5 of a computed one.
         double best = 1e300;
         int best_n = 1;
-        const int lo = std::max(1, (nzmax + 71) / 72);
+        const int cap = ti.zcap > 0 ? ti.zcap : 72;
+        const int lo = std::max(1, (nzmax + cap - 1) / cap);
         const int hi = std::max(lo, nzmax / 16);
         for (int nzc = lo; nzc <= hi; ++nzc) {
             long long n = ncols * nzc;

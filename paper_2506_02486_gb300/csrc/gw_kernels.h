@@ -19,6 +19,7 @@ struct TileInfo {
     int tx, ty;        // tile extent in x and y (interior points)
     int threads;       // threads per CTA
     size_t smem;       // dynamic shared memory bytes
+    int zcap;          // most planes per work item
 };
 
 // Tile configurations available for a storage type (ids 0..n-1).
