@@ -438,6 +438,15 @@ gw_status gw_server_stats_get(gw_server *s, gw_server_stats *out);
 /* Server clock in seconds (the clock of gw_result). */
 double gw_server_now(gw_server *s);
 
+/* Failure-detection self-test: one warp waits on an mbarrier nobody
+ * arrives on and on a device counter nobody increments -- the two kinds of
+ * wait of the step kernel -- each bounded by limit_us (1 us .. 2 s; the
+ * step kernel bounds them by 4 s).  *expired receives one bit per wait that
+ * gave up (1: mbarrier, 2: counter).  Returns GW_ERR_TIMEOUT when a wait
+ * gave up (the expected outcome); the context stays usable.  Synchronises
+ * the legacy stream. */
+gw_status gw_selftest_timeout(gw_ctx *ctx, unsigned limit_us, int *expired);
+
 /* Record the device time of every step-kernel launch (CUDA events) while
  * enabled; gw_kernel_stats_get returns the totals and resets them. */
 gw_status gw_kernel_timing(gw_domain *d, int enable);

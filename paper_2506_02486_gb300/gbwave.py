@@ -167,6 +167,7 @@ _SIGS = {
     "gw_wait": [_P, _U64, _I, ctypes.POINTER(gw_result)],
     "gw_server_stats_get": [_P, ctypes.POINTER(gw_server_stats)],
     "gw_server_now": [_P],
+    "gw_selftest_timeout": [_P, ctypes.c_uint, ctypes.POINTER(_I)],
     "gw_state_bytes": [_P, ctypes.POINTER(_SZ)],
     "gw_save_state": [_P, _P],
     "gw_load_state": [_P, _P],
@@ -597,6 +598,14 @@ def gw_server_stats_get(srv: int) -> dict:
 
 def gw_server_now(srv: int) -> float:
     return float(lib().gw_server_now(srv))
+
+
+def gw_selftest_timeout(ctx: int, limit_us: int) -> tuple[int, int]:
+    """(status, expired bits): GW_ERR_TIMEOUT with bits 3 is the expected
+    outcome (both device waits gave up)."""
+    bits = _I()
+    st = lib().gw_selftest_timeout(ctx, int(limit_us), ctypes.byref(bits))
+    return st, bits.value
 
 
 def gw_state_bytes(dom: int) -> int:

@@ -230,3 +230,12 @@ def test_domain_bytes_bounds_the_fields(lib):
         assert gw.gw_domain_bytes(d2, nrec=64) > b + 64 * 990 * 4
     with pytest.raises(gw.GWError):
         gw.gw_domain_bytes(gw.shot_desc(0, 8, 8))
+
+
+def test_selftest_needs_a_device_context(lib):
+    ctx = gw.gw_ctx_create(-1)
+    try:
+        st, bits = gw.gw_selftest_timeout(ctx, 1000)
+        assert st == gw.GW_ERR_STATE and bits == 0
+    finally:
+        gw.gw_ctx_destroy(ctx)
