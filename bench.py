@@ -353,7 +353,7 @@ BATCH_CHUNK = 25
 
 def run_batch(dtype="f32", *, seed=BATCH_SEED, steps=BATCH_STEPS,
               chunk=BATCH_CHUNK, autotune=True, persistent=True,
-              sequential=False, warmup=BATCH_CHUNK):
+              sequential=False, warmup=BATCH_CHUNK, tile=0):
     """64 independent cubic shots (sides drawn from {96..256} step 16, each
     with its own layered model and source, 20-cell sponge, 20 Hz) advanced
     together: one launch per tile group per K-step chunk, chunks replayed
@@ -384,7 +384,7 @@ def run_batch(dtype="f32", *, seed=BATCH_SEED, steps=BATCH_STEPS,
             for b in plan:
                 s = Shot(seg, b.side, b.side, b.side, nsteps=steps + warmup,
                          dtype=dtype, sponge=b.sponge,
-                         tile=tiles.get(b.side, 0))
+                         tile=tiles.get(b.side, tile))
                 shots.append(s)
                 s.set_model(b.model())
                 s.add_ricker(b.source, 20.0)

@@ -32,7 +32,7 @@ def nvcc() -> str:
 
 
 # stencil_inst.cu is compiled once per tile configuration (-DGW_INST=i)
-NUM_INST = 16
+NUM_INST = 18
 INST_SRC = os.path.join(CSRC, "stencil_inst.cu")
 
 

@@ -10,7 +10,7 @@ namespace gw {
     TileInfo step_info_##I();
 GW_DECL(0) GW_DECL(1) GW_DECL(2) GW_DECL(3) GW_DECL(4) GW_DECL(5)
 GW_DECL(6) GW_DECL(7) GW_DECL(8) GW_DECL(9) GW_DECL(10) GW_DECL(11)
-GW_DECL(12) GW_DECL(13) GW_DECL(14) GW_DECL(15)
+GW_DECL(12) GW_DECL(13) GW_DECL(14) GW_DECL(15) GW_DECL(16) GW_DECL(17)
 #undef GW_DECL
 
 namespace {
@@ -29,7 +29,7 @@ const Entry kTable[] = {
     GW_E(7, DT_F16S, 0), GW_E(6, DT_F16S, 1),  GW_E(8, DT_F16S, 2),
     GW_E(10, DT_BF16, 0), GW_E(9, DT_BF16, 1), GW_E(11, DT_BF16, 2),
     GW_E(12, DT_F32, 4), GW_E(13, DT_F32, 5),  GW_E(14, DT_F32, 6),
-    GW_E(15, DT_F16S, 3),
+    GW_E(15, DT_F16S, 3), GW_E(16, DT_F16S, 4), GW_E(17, DT_BF16, 3),
 };
 #undef GW_E
 

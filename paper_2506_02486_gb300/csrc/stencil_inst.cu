@@ -44,6 +44,10 @@ using C = Cfg<float, 64, 14, 1, 8, 4, 2, true>;   constexpr bool kDelta = false;
 using C = Cfg<float, 128, 7, 1, 8, 4, 2, true>;   constexpr bool kDelta = false;
 #elif GW_INST == 15
 using C = Cfg<__half, 64, 14, 1, 8, 4, 2, true>;  constexpr bool kDelta = true;
+#elif GW_INST == 16
+using C = Cfg<__half, 32, 56, 2, 8, 4>;           constexpr bool kDelta = true;
+#elif GW_INST == 17
+using C = Cfg<__nv_bfloat16, 32, 56, 2, 8, 4>;    constexpr bool kDelta = true;
 #else
 #error "unknown configuration index"
 #endif
