@@ -368,6 +368,12 @@ gw_status gw_autotune(gw_ctx *ctx, const gw_shot_desc *desc, int px, int py,
  * per-shape timings do not see.  tiles_out[i] receives shot i's tile. */
 gw_status gw_plan_tiles(gw_ctx *ctx, int n, const gw_shot_desc *descs, int steps,
                         double margin, int *tiles_out);
+/* Tile model (host only, no timing): the tile expected to move the fewest
+ * bytes per point for an nx x ny plane -- the staged plane's x/y halo
+ * overhead plus the two pointwise fields, times the waste of partial tiles
+ * at the grid edges -- among each type's main tiles.  The server uses it
+ * for requests whose tile is 0. */
+gw_status gw_pick_tile(int dtype, int nx, int ny, int *tile);
 /* Number of kernel tiles available for a storage type (GW_F32 ...). */
 gw_status gw_tile_count(int dtype, int *count);
 

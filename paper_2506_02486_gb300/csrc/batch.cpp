@@ -368,6 +368,14 @@ gw_status gw_batch_stats_get(gw_batch *b, gw_kernel_stats *out)
 
 }  // extern "C"
 
+extern "C" gw_status gw_pick_tile(int dtype, int nx, int ny, int *tile)
+{
+    if (!tile || dtype < 0 || dtype > 3 || nx <= 0 || ny <= 0)
+        return fail(GW_ERR_ARG, "bad tile-model arguments");
+    *tile = step_cfg_pick(dtype, nx, ny) + 1;
+    return GW_OK;
+}
+
 extern "C" gw_status gw_tile_count(int dtype, int *count)
 {
     if (!count || dtype < 0 || dtype > 3) return fail(GW_ERR_ARG, "bad storage type");

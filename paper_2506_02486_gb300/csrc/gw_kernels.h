@@ -24,6 +24,9 @@ struct TileInfo {
 
 // Tile configurations available for a storage type (ids 0..n-1).
 int step_cfg_count(int dtype);
+// The tile (id) the shape model expects to move the fewest bytes per point
+// for an nx x ny plane: halo overhead of the tile times partial-tile waste.
+int step_cfg_pick(int dtype, int nx, int ny);
 bool step_cfg_info(int dtype, int cfg, TileInfo *out);
 // Max resident CTAs per SM of a configuration (after opting in to its
 // shared memory); 0 on error.

@@ -104,6 +104,7 @@ gw_status setup(gw_server *S, Req *q)
 {
     q->res.admit_s = S->now();
     gw_shot_desc d = q->r.desc;
+    if (d.tile == 0) GW_TRY(gw_pick_tile(d.dtype, d.nx, d.ny, &d.tile));
     GW_TRY(gw_domain_create(S->ctx, &d, 1, 1, 1, nullptr, nullptr, nullptr, 1, &q->dom));
     if (q->r.vel) GW_TRY(gw_set_model_f32(q->dom, q->r.vel));
     else GW_TRY(gw_set_model_layered(q->dom, q->vz.data()));

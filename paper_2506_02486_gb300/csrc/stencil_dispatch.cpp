@@ -16,22 +16,25 @@ GW_DECL(12) GW_DECL(13) GW_DECL(14) GW_DECL(15) GW_DECL(16) GW_DECL(17)
 namespace {
 struct Entry {
     int dtype, id;
+    bool pick;     // offered to the shape model (step_cfg_pick)
     cudaError_t (*launch)(bool, int, const StepArgs &, cudaStream_t);
     int (*occ)(bool);
     TileInfo (*info)();
 };
-#define GW_E(I, D, ID) {D, ID, step_launch_##I, step_occ_##I, step_info_##I}
+#define GW_E(I, D, ID) {D, ID, false, step_launch_##I, step_occ_##I, step_info_##I}
+#define GW_P(I, D, ID) {D, ID, true, step_launch_##I, step_occ_##I, step_info_##I}
 // id 0 of each storage type is its default tile: the fastest on the 512^3
 // layered shot (FP32 64x28 with a 10-slot ring, 16-bit 128x14).
 const Entry kTable[] = {
-    GW_E(3, DT_F32, 0),  GW_E(1, DT_F32, 1),   GW_E(2, DT_F32, 2),
-    GW_E(0, DT_F32, 3),  GW_E(4, DT_F64, 0),   GW_E(5, DT_F64, 1),
-    GW_E(7, DT_F16S, 0), GW_E(6, DT_F16S, 1),  GW_E(8, DT_F16S, 2),
-    GW_E(10, DT_BF16, 0), GW_E(9, DT_BF16, 1), GW_E(11, DT_BF16, 2),
+    GW_P(3, DT_F32, 0),  GW_P(1, DT_F32, 1),   GW_P(2, DT_F32, 2),
+    GW_E(0, DT_F32, 3),  GW_P(4, DT_F64, 0),   GW_P(5, DT_F64, 1),
+    GW_P(7, DT_F16S, 0), GW_P(6, DT_F16S, 1),  GW_E(8, DT_F16S, 2),
+    GW_P(10, DT_BF16, 0), GW_P(9, DT_BF16, 1), GW_E(11, DT_BF16, 2),
     GW_E(12, DT_F32, 4), GW_E(13, DT_F32, 5),  GW_E(14, DT_F32, 6),
-    GW_E(15, DT_F16S, 3), GW_E(16, DT_F16S, 4), GW_E(17, DT_BF16, 3),
+    GW_E(15, DT_F16S, 3), GW_P(16, DT_F16S, 4), GW_P(17, DT_BF16, 3),
 };
 #undef GW_E
+#undef GW_P
 
 const Entry *find(int dtype, int id)
 {
@@ -57,6 +60,29 @@ bool step_cfg_info(int dtype, int cfg, TileInfo *out)
     // ~86 (1024 x 1024 x 512: 362 against 336 Gpts/s with 64)
     out->zcap = dtype_size(dtype) == 2 ? 96 : 72;
     return true;
+}
+
+int step_cfg_pick(int dtype, int nx, int ny)
+{
+    // bytes moved per useful point, up to a constant: the staged u plane
+    // with its x/y halo plus the two pointwise fields, times the share of
+    // the grid the partial tiles cover
+    const int hl = dtype_size(dtype) == 2 ? 8 : 4;
+    double best = 1e300;
+    int id = 0;
+    for (const Entry &e : kTable) {
+        if (e.dtype != dtype || !e.pick) continue;
+        const TileInfo t = e.info();
+        const double halo = (double)(t.tx + 2 * hl) * (t.ty + 2 * R) / ((double)t.tx * t.ty);
+        const double pad = (double)((nx + t.tx - 1) / t.tx * t.tx) *
+                           ((ny + t.ty - 1) / t.ty * t.ty) / ((double)nx * ny);
+        const double cost = (halo + 2.0) * pad;
+        if (cost < best * (1.0 - 1e-9)) {   // ties: the earlier (default) tile
+            best = cost;
+            id = e.id;
+        }
+    }
+    return id;
 }
 
 int step_cfg_occupancy(int dtype, int cfg, bool sponge)

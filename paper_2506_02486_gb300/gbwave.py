@@ -160,6 +160,7 @@ _SIGS = {
     "gw_autotune": [_P, ctypes.POINTER(gw_shot_desc), _I, _I, _I, _I,
                     ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _I],
     "gw_tile_count": [_I, ctypes.POINTER(_I)],
+    "gw_pick_tile": [_I, _I, _I, ctypes.POINTER(_I)],
     "gw_plan_tiles": [_P, _I, _P, _I, _D, _P],
     "gw_server_create": [_P, _SZ, _I, _I, ctypes.POINTER(_P)],
     "gw_server_destroy": [_P],
@@ -526,6 +527,14 @@ def gw_batch_stats_get(b: int) -> dict:
     _check(lib().gw_batch_stats_get(b, ctypes.byref(s)), "gw_batch_stats_get")
     return {"launches": s.launches, "total_ms": s.total_ms,
             "halo_ms": s.halo_ms}
+
+
+def gw_pick_tile(dtype, nx: int, ny: int) -> int:
+    t = _I()
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    _check(lib().gw_pick_tile(dt, int(nx), int(ny), ctypes.byref(t)),
+           "gw_pick_tile")
+    return t.value
 
 
 def gw_tile_count(dtype) -> int:

@@ -239,3 +239,17 @@ def test_selftest_needs_a_device_context(lib):
         assert st == gw.GW_ERR_STATE and bits == 0
     finally:
         gw.gw_ctx_destroy(ctx)
+
+
+def test_tile_model_prefers_fitting_tiles(lib):
+    """The host-side tile model: the default tile on a large grid that it
+    tiles well, a 32-wide tile where 64-wide tiles would leave half-empty
+    columns, and only the type's own tiles."""
+    assert gw.gw_pick_tile("f32", 512, 512) == 1            # 64 x 28
+    assert gw.gw_pick_tile("f32", 96, 96) == 3              # 32 x 56
+    assert gw.gw_pick_tile("bf16", 96, 112) == 4            # 32 x 56
+    for dt in ("f32", "f64", "f16s", "bf16"):
+        for n in (17, 64, 100, 333):
+            assert 1 <= gw.gw_pick_tile(dt, n, n) <= gw.gw_tile_count(dt)
+    with pytest.raises(gw.GWError):
+        gw.gw_pick_tile("f32", 0, 8)
