@@ -327,16 +327,18 @@ gw_status gw_check_fields_noalloc(const void *u_cur, const void *u_prev,
 /* ------------------------------------------------------------------ */
 /* batches: several independent shots advanced by the same launches    */
 
-/* Group nshots existing domains of one context (one storage type; fused or
- * no halos) so that every launch covers the work items of all of them:
- * shots with the same kernel tile share one launch per step (or per chunk
- * in persistent mode); shots with different tiles form separate groups
- * launched one after the other.  Each shot keeps its own model, sources,
- * receivers, step counter and logs, read through its domain.  chunk: steps
- * per CUDA-graph chunk (0: 25; < 0: plain launches).  persistent != 0: one
- * cooperative launch per chunk with a device-wide barrier between steps.
- * The batch allocates its tables from the segment; destroy it before its
- * domains. */
+/* Group nshots existing domains of one context (one storage type) so that
+ * every launch covers the work items of all of them: shots with the same
+ * kernel tile, sponge setting, address mode and halo mode share one launch
+ * per step (or per chunk in persistent mode); shots that differ form
+ * separate groups launched one after the other.  Shots with separate halo
+ * copies (GW_HALO_SEPARATE) run one launch per step followed by their
+ * halo-copy kernels, whatever `persistent` says.  Each shot keeps its own
+ * model, sources, receivers, step counter and logs, read through its
+ * domain.  chunk: steps per CUDA-graph chunk (0: 25; < 0: plain launches).
+ * persistent != 0: one cooperative launch per chunk with a device-wide
+ * barrier between steps.  The batch allocates its tables from the segment;
+ * destroy it before its domains. */
 gw_status gw_batch_create(gw_ctx *ctx, int nshots, gw_domain *const *shots,
                           int chunk, int persistent, gw_batch **out);
 gw_status gw_batch_destroy(gw_batch *b);

@@ -20,6 +20,7 @@ struct Group {
     int cfg = 0;
     bool sponge = false;
     bool symmetric = true;
+    bool separate = false;      // halos copied by a kernel after each step
     TileInfo ti{};
     std::vector<gw_domain *> doms;
     std::vector<SubDev> subs;
@@ -137,7 +138,7 @@ StepArgs group_args(gw_batch *b, Group &g, int k)
     a.nk = 1;
     a.gbar = g.d_gbar;
     a.symmetric = g.symmetric ? 1 : 0;
-    a.fused_halo = 1;
+    a.fused_halo = g.separate ? 0 : 1;
     return a;
 }
 
@@ -164,7 +165,17 @@ gw_status enqueue_group(gw_batch *b, Group &g, int nk, cudaStream_t s, bool time
         }
         return GW_OK;
     };
-    if (b->persistent && nk > 1) {
+    if (g.separate) {
+        // step, then the face-halo copies of every decomposed member; the
+        // copies read the member's step counter like its own launches do
+        for (int k = 0; k < nk; ++k) {
+            GW_TRY(launch(group_args(b, g, k), 1));
+            for (gw_domain *d : g.doms)
+                if (!d->halo.empty())
+                    GW_TRY_CUDA(launch_halo(d->d_halo, (int)d->halo.size(), d->halo_units,
+                                            d->d_subs, d->d_step, k, d->dtype, s));
+        }
+    } else if (b->persistent && nk > 1) {
         GW_TRY_CUDA(cudaMemsetAsync(g.d_gbar, 0, sizeof(unsigned), s));
         StepArgs a = group_args(b, g, 0);
         a.nk = nk;
@@ -236,22 +247,24 @@ gw_status gw_batch_create(gw_ctx *c, int nshots, gw_domain *const *shots, int ch
         else if (d->ctx != c) st = fail(GW_ERR_ARG, "shot %d belongs to another context", i);
         else if (d->dtype != b->dtype) st = fail(GW_ERR_ARG, "shots must share one storage type");
         else if (!d->model_set) st = fail(GW_ERR_STATE, "shot %d has no model", i);
-        else if (d->desc.halo_mode == GW_HALO_SEPARATE && !d->halo.empty())
-            st = fail(GW_ERR_ARG, "shot %d uses separate halo puts", i);
         if (st != GW_OK) {
             delete b;
             return st;
         }
         const bool sponge = d->desc.sponge > 0;
+        const bool separate = d->desc.halo_mode == GW_HALO_SEPARATE && !d->halo.empty();
         Group *g = nullptr;
         for (Group &q : b->groups)
-            if (q.cfg == d->cfg && q.sponge == sponge && q.symmetric == d->symmetric) g = &q;
+            if (q.cfg == d->cfg && q.sponge == sponge && q.symmetric == d->symmetric &&
+                q.separate == separate)
+                g = &q;
         if (!g) {
             b->groups.emplace_back();
             g = &b->groups.back();
             g->cfg = d->cfg;
             g->sponge = sponge;
             g->symmetric = d->symmetric;
+            g->separate = separate;
             g->ti = d->ti;
         }
         g->doms.push_back(d);
