@@ -264,8 +264,9 @@ def run_reference(args, world, rank, pg):
         "ms_per_step": el / max(1, args.steps) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "layered_512cubed (per step: one slab)",
-                   "slab": [n, n, nz], "sponge": shot.sponge},
+        "config": {"workload": "layered_512cubed", "grid": [n, n, n],
+                   "sponge": shot.sponge, "source_hz": shot.f_peak,
+                   "slab_per_step": [n, n, nz]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
                          "kind": "oracle",
                          "sample": f"{n}x{n}x{nz} slab of the 512^3 layered "
