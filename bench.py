@@ -516,6 +516,8 @@ def run_ours(args, world, rank, local, pg):
             "frac": achieved / peak, "traffic": traffic,
             "peak_kind": peak_kind,
             "alg_bytes_per_launch": ALG_BYTES_PER_POINT * npts,
+            "alg_bytes_per_point": ALG_BYTES_PER_POINT,
+            "dram_bytes_per_point": (traffic / npts) if traffic else None,
             "kernel_ms": kavg_ms,
         },
         "e2e": {"value": e2e_value, "unit": UNIT,
