@@ -469,10 +469,13 @@ def run_ours(args, world, rank, local, pg):
                 vms, vstats, _, _, _ = run_shot_device(
                     segv, shot, vs, args.warmup, **kw)
                 kavg = vstats["total_ms"] / max(1, vstats["launches"])
+                bpp = 10 if kw.get("dtype") in ("f16s", "bf16") else 16
                 variants[name] = {
                     "gpts": npts * vs / (vms * 1e-3) / 1e9,
                     "kernel_ms": kavg,
                     "halo_kernel_ms": vstats["halo_ms"] / max(1, vstats["launches"]),
+                    "alg_bytes_per_point": bpp,
+                    "roofline_frac": bpp * npts / (kavg * 1e-3) / 1e9 / measured_peak()[0],
                     "steps": vs,
                 }
             for dt in ("f32", "bf16"):
