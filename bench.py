@@ -358,13 +358,15 @@ BATCH_CHUNK = 25
 
 
 def run_batch(dtype="f32", *, seed=BATCH_SEED, steps=BATCH_STEPS,
-              chunk=BATCH_CHUNK, autotune=True, persistent=True,
-              sequential=False, warmup=BATCH_CHUNK, tile=0):
+              chunk=BATCH_CHUNK, autotune=True, persistent=False,
+              sequential=False, warmup=BATCH_CHUNK, tile=0, margin=0.0,
+              tiles_by="plan"):
     """64 independent cubic shots (sides drawn from {96..256} step 16, each
     with its own layered model and source, 20-cell sponge, 20 Hz) advanced
-    together: one launch per tile group per K-step chunk, chunks replayed
-    from CUDA graphs, tiles per grid side from the autotuner.  Returns a
-    dict of aggregate Gpts/s and the schedule."""
+    together: tiles per grid side from the autotuner, one launch per tile
+    group per step with the groups side by side, K-step chunks replayed
+    from one CUDA graph (or, persistent, one cooperative launch per group
+    per chunk).  Returns a dict of aggregate Gpts/s and the schedule."""
     import torch
     import workloads
     from paper_2506_02486_gb300 import gbwave as gw
@@ -378,10 +380,13 @@ def run_batch(dtype="f32", *, seed=BATCH_SEED, steps=BATCH_STEPS,
     with Segment(total + (2 << 30)) as seg:
         tiles = {}
         t0 = time.perf_counter()
-        if autotune:
+        if autotune and tiles_by == "model":
+            for b in plan:
+                tiles[b.side] = gw.gw_pick_tile(dtype, b.side, b.side)
+        elif autotune:
             descs = [gw.shot_desc(b.side, b.side, b.side, nsteps=steps,
                                   dtype=dtype, sponge=b.sponge) for b in plan]
-            for b, t in zip(plan, gw.gw_plan_tiles(seg.ctx, descs, 20, 0.1)):
+            for b, t in zip(plan, gw.gw_plan_tiles(seg.ctx, descs, 20, margin)):
                 tiles[b.side] = t
         out["autotune_s"] = time.perf_counter() - t0
         out["tiles"] = {str(k): v for k, v in tiles.items()}
@@ -479,11 +484,12 @@ def run_ours(args, world, rank, local, pg):
                     "steps": vs,
                 }
             for dt in ("f32", "bf16"):
-                r = run_batch(dt)
-                variants[f"batch64_{dt}"] = {
-                    k: r[k] for k in ("gpts", "ms", "steps", "chunk",
-                                      "points", "groups", "ctas", "seed",
-                                      "autotune_s", "persistent")}
+                for suffix, kw in (("", {}), ("_persistent", dict(persistent=True))):
+                    r = run_batch(dt, **kw)
+                    variants[f"batch64_{dt}{suffix}"] = {
+                        k: r[k] for k in ("gpts", "ms", "steps", "chunk",
+                                          "points", "groups", "ctas", "seed",
+                                          "autotune_s", "persistent")}
     finally:
         seg.close()
         seg1.close()
@@ -621,10 +627,11 @@ def run_batch_modes(args):
     buildlib.build()
     torch.cuda.set_device(0)
     for dt in ("f32", "bf16"):
-        for name, kw in (("batch_persistent_tuned", {}),
-                         ("batch_per_step_tuned", dict(persistent=False)),
-                         ("batch_persistent_default_tile",
-                          dict(autotune=False)),
+        for name, kw in (("batch_graphs_tuned_side_by_side", {}),
+                         ("batch_persistent_tuned", dict(persistent=True)),
+                         ("batch_graphs_uniform_tile", dict(margin=1.0)),
+                         ("batch_graphs_tile_model", dict(tiles_by="model")),
+                         ("batch_graphs_default_tile", dict(autotune=False)),
                          ("sequential_shots_tuned", dict(sequential=True))):
             r = run_batch(dt, **kw)
             r["schedule"] = name

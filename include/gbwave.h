@@ -431,7 +431,7 @@ typedef struct gw_server_stats {
 } gw_server_stats;
 
 /* max_slots: most shots resident at once; chunk: steps per batch chunk
- * (0: 25).  The server uses a non-blocking stream of its own. */
+ * (0: 25).  The server runs each storage type on a non-blocking stream of its own. */
 gw_status gw_server_create(gw_ctx *ctx, size_t hbm_budget, int max_slots, int chunk,
                            gw_server **out);
 /* Stops the loop after the running chunk; shots not finished end with

@@ -35,7 +35,6 @@ struct Group {
     unsigned *d_gbar = nullptr;
     unsigned *err = nullptr;    // the first shot's device error word
     int grid = 0;
-    cudaGraphExec_t gexec = nullptr;
 };
 
 }  // namespace
@@ -48,6 +47,13 @@ struct gw_batch {
     bool persistent = false;
     std::vector<Group> groups;
     cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;          // one chunk of every group
+    // groups launched side by side within a chunk (non-persistent batches
+    // of more than one group): streams forked from the caller's and joined
+    // at the end of the chunk
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
     std::vector<int> ev_steps;
@@ -188,12 +194,48 @@ gw_status enqueue_group(gw_batch *b, Group &g, int nk, cudaStream_t s, bool time
     return GW_OK;
 }
 
-gw_status ensure_graph(gw_batch *b, Group &g)
+// One chunk of nk steps of every group on stream s.  Groups of a
+// non-persistent batch run side by side on forked streams (different tiles
+// mean different kernels; side by side, one group's tail CTAs leave no SM
+// idle); persistent groups and timed chunks run one after the other.
+gw_status enqueue_all(gw_batch *b, int nk, cudaStream_t s, bool timed)
 {
-    if (g.gexec) return GW_OK;
+    const size_t ng = b->groups.size();
+    if (ng > 1 && !b->persistent && !timed) {
+        if (b->aux.size() < ng - 1) {
+            if (!b->fork) GW_TRY_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+            while (b->aux.size() < ng - 1) {
+                cudaStream_t a = nullptr;
+                cudaEvent_t e = nullptr;
+                GW_TRY_CUDA(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+                b->aux.push_back(a);
+                GW_TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                b->joins.push_back(e);
+            }
+        }
+        GW_TRY_CUDA(cudaEventRecord(b->fork, s));
+        for (size_t gi = 1; gi < ng; ++gi) {
+            cudaStream_t a = b->aux[gi - 1];
+            GW_TRY_CUDA(cudaStreamWaitEvent(a, b->fork, 0));
+            GW_TRY(enqueue_group(b, b->groups[gi], nk, a, false, false));
+            GW_TRY_CUDA(cudaEventRecord(b->joins[gi - 1], a));
+        }
+        GW_TRY(enqueue_group(b, b->groups[0], nk, s, false, false));
+        for (size_t gi = 1; gi < ng; ++gi)
+            GW_TRY_CUDA(cudaStreamWaitEvent(s, b->joins[gi - 1], 0));
+        return GW_OK;
+    }
+    for (size_t gi = 0; gi < ng; ++gi)
+        GW_TRY(enqueue_group(b, b->groups[gi], nk, s, timed, gi == 0));
+    return GW_OK;
+}
+
+gw_status ensure_graph(gw_batch *b)
+{
+    if (b->gexec) return GW_OK;
     if (!b->cap) GW_TRY_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
     GW_TRY_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    gw_status st = enqueue_group(b, g, b->chunk, b->cap, false, false);
+    gw_status st = enqueue_all(b, b->chunk, b->cap, false);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
     if (st != GW_OK) {
@@ -201,7 +243,7 @@ gw_status ensure_graph(gw_batch *b, Group &g)
         return st;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&g.gexec, graph, 0);
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     return GW_OK;
@@ -287,10 +329,12 @@ gw_status gw_batch_destroy(gw_batch *b)
     cudaSetDevice(b->ctx->device);
     cudaDeviceSynchronize();
     harvest(b);
-    for (Group &g : b->groups) {
-        if (g.gexec) cudaGraphExecDestroy(g.gexec);
+    for (Group &g : b->groups)
         if (g.g_meta) ctx_free(b->ctx, g.g_meta);
-    }
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (cudaStream_t a : b->aux) cudaStreamDestroy(a);
+    for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
     return GW_OK;
@@ -324,14 +368,11 @@ gw_status gw_batch_step(gw_batch *b, int nsteps, gw_stream stream)
     while (left > 0) {
         const bool whole = b->graphs && !b->timing && left >= b->chunk;
         const int nk = whole ? b->chunk : std::min(left, b->chunk);
-        for (size_t gi = 0; gi < b->groups.size(); ++gi) {
-            Group &g = b->groups[gi];
-            if (whole) {
-                GW_TRY(ensure_graph(b, g));
-                GW_TRY_CUDA(cudaGraphLaunch(g.gexec, s));
-            } else {
-                GW_TRY(enqueue_group(b, g, nk, s, b->timing, gi == 0));
-            }
+        if (whole) {
+            GW_TRY(ensure_graph(b));
+            GW_TRY_CUDA(cudaGraphLaunch(b->gexec, s));
+        } else {
+            GW_TRY(enqueue_all(b, nk, s, b->timing));
         }
         left -= nk;
     }

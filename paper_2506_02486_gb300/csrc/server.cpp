@@ -2,7 +2,8 @@
 // GPU work: it admits submitted shots in arrival order while they fit the
 // HBM budget and a slot, sets them up (legacy-stream copies, overlapped
 // with the running chunk), advances every resident shot with one multi-shot
-// batch per storage type on its own non-blocking stream, and retires shots
+// batch per storage type, each on a non-blocking stream of its own (tile
+// groups side by side within it), and retires shots
 // at chunk boundaries (traces to the caller's buffer, final check).
 #include <algorithm>
 #include <chrono>
@@ -39,7 +40,7 @@ struct gw_server {
     size_t budget = 0;
     int slots = 0;
     int chunk = kDefaultChunk;
-    cudaStream_t stream = nullptr;
+    cudaStream_t streams[4] = {nullptr, nullptr, nullptr, nullptr};  // one per storage type
     Clock::time_point t0;
     std::thread th;
 
@@ -163,9 +164,10 @@ gw_status rebuild(gw_server *S)
         for (Req *q : S->active)
             if (q->r.desc.dtype == t) doms.push_back(q->dom);
         if (doms.empty()) continue;
-        // persistent chunks without graphs: membership changes too often
-        // for captured graphs to pay off
-        GW_TRY(gw_batch_create(S->ctx, (int)doms.size(), doms.data(), -S->chunk, 1,
+        // plain per-step launches, tile groups side by side: membership
+        // changes too often for captured graphs to pay off, and persistent
+        // (cooperative) groups would have to run one after the other
+        GW_TRY(gw_batch_create(S->ctx, (int)doms.size(), doms.data(), -S->chunk, 0,
                                &S->batch[t]));
     }
     std::lock_guard<std::mutex> lk(S->mu);
@@ -224,8 +226,9 @@ void loop(gw_server *S)
         }
         const double t_launch = S->now();
         gw_status st = GW_OK;
-        for (gw_batch *b : S->batch)
-            if (b && st == GW_OK) st = gw_batch_step(b, K, S->stream);
+        // the storage types' batches run side by side, one stream each
+        for (int t = 0; t < 4; ++t)
+            if (S->batch[t] && st == GW_OK) st = gw_batch_step(S->batch[t], K, S->streams[t]);
         // while the chunk runs: admit and set up the next shots
         std::vector<Req *> joiners;
         if (st == GW_OK) {
@@ -235,7 +238,11 @@ void loop(gw_server *S)
             }
             if (!adm.empty()) joiners = setup_all(S, adm, true);
         }
-        cudaError_t e = cudaStreamSynchronize(S->stream);
+        cudaError_t e = cudaSuccess;
+        for (cudaStream_t x : S->streams) {
+            cudaError_t ex = cudaStreamSynchronize(x);
+            if (e == cudaSuccess) e = ex;
+        }
         if (st == GW_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
         {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -267,7 +274,7 @@ void loop(gw_server *S)
         S->st.max_active = std::max(S->st.max_active, (int)S->active.size());
     }
     // stopped: nothing runs any more
-    cudaStreamSynchronize(S->stream);
+    for (cudaStream_t x : S->streams) cudaStreamSynchronize(x);
     for (gw_batch *&b : S->batch) {
         if (b) gw_batch_destroy(b);
         b = nullptr;
@@ -306,7 +313,8 @@ gw_status gw_server_create(gw_ctx *c, size_t hbm_budget, int max_slots, int chun
     S->chunk = chunk == 0 ? kDefaultChunk : chunk;
     S->st.budget_bytes = hbm_budget;
     cudaError_t e = cudaSetDevice(c->device);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    for (int t = 0; t < 4 && e == cudaSuccess; ++t)
+        e = cudaStreamCreateWithFlags(&S->streams[t], cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete S;
         return cuda_fail(e, "cudaStreamCreateWithFlags");
@@ -315,7 +323,8 @@ gw_status gw_server_create(gw_ctx *c, size_t hbm_budget, int max_slots, int chun
     try {
         S->th = std::thread(loop, S);
     } catch (...) {
-        cudaStreamDestroy(S->stream);
+        for (cudaStream_t x : S->streams)
+            if (x) cudaStreamDestroy(x);
         delete S;
         return fail(GW_ERR_NOMEM, "cannot start the server thread");
     }
@@ -333,7 +342,8 @@ gw_status gw_server_destroy(gw_server *S)
     S->cv_work.notify_all();
     if (S->th.joinable()) S->th.join();
     for (auto &kv : S->done) delete kv.second;
-    cudaStreamDestroy(S->stream);
+    for (cudaStream_t x : S->streams)
+        if (x) cudaStreamDestroy(x);
     delete S;
     return GW_OK;
 }
