@@ -209,12 +209,15 @@ def cpu_oracle_rate(shot, target_s: float, nthreads: int) -> tuple[float, str]:
     z0 = max(0, min(n - nz, shot.src[2] - nz // 2))
     slab = np.ascontiguousarray(shot.vel[z0:z0 + nz])
     src = (shot.src[0], shot.src[1], shot.src[2] - z0)
-    # one step to size the timed run to ~target_s (the probe overestimates)
-    t = time.perf_counter()
-    oracle.run(slab, shot.h, 1, dt=dt, src=src, f_peak=shot.f_peak,
-               sponge=shot.sponge, nthreads=nthreads)
-    one = time.perf_counter() - t
-    steps = int(max(2, min(200, round(target_s / max(one, 1e-3)))))
+    # size the timed run to ~target_s from the difference of a 1-step and
+    # a 3-step run (a run has a set-up cost several steps long)
+    def timed(k):
+        t = time.perf_counter()
+        oracle.run(slab, shot.h, k, dt=dt, src=src, f_peak=shot.f_peak,
+                   sponge=shot.sponge, nthreads=nthreads)
+        return time.perf_counter() - t
+    per_step = max((timed(3) - timed(1)) / 2, 1e-4)
+    steps = int(max(2, min(2000, round(target_s / per_step))))
     t = time.perf_counter()
     oracle.run(slab, shot.h, steps, dt=dt, src=src, f_peak=shot.f_peak,
                sponge=shot.sponge, nthreads=nthreads)
