@@ -336,9 +336,11 @@ gw_status gw_check_fields_noalloc(const void *u_cur, const void *u_prev,
  * halo-copy kernels, whatever `persistent` says.  Each shot keeps its own
  * model, sources, receivers, step counter and logs, read through its
  * domain.  chunk: steps per CUDA-graph chunk (0: 25; < 0: plain launches).
- * persistent != 0: one cooperative launch per chunk with a device-wide
- * barrier between steps.  The batch allocates its tables from the segment;
- * destroy it before its domains. */
+ * persistent != 0: one cooperative launch per group per chunk with a
+ * device-wide barrier between steps, groups one after the other; otherwise
+ * the groups of a chunk run side by side on streams forked from the
+ * caller's and joined at the chunk's end (one graph per chunk).  The batch
+ * allocates its tables from the segment; destroy it before its domains. */
 gw_status gw_batch_create(gw_ctx *ctx, int nshots, gw_domain *const *shots,
                           int chunk, int persistent, gw_batch **out);
 gw_status gw_batch_destroy(gw_batch *b);
