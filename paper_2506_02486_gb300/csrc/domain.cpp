@@ -199,6 +199,20 @@ gw_status plan_schedule(gw_domain *d)
 // streams (which do not wait for the legacy stream) see them.
 gw_status push_shot(gw_domain *d)
 {
+    // bounding box of the sources and receivers: items outside it skip the
+    // per-item search for them
+    for (int a = 0; a < 3; ++a) {
+        d->shot.lo[a] = 1 << 30;
+        d->shot.hi[a] = -1;
+    }
+    for (const std::vector<int4> *l : {&d->srcs, &d->recs})
+        for (const int4 &q : *l) {
+            const int c[3] = {q.x, q.y, q.z};
+            for (int a = 0; a < 3; ++a) {
+                d->shot.lo[a] = std::min(d->shot.lo[a], c[a]);
+                d->shot.hi[a] = std::max(d->shot.hi[a], c[a]);
+            }
+        }
     GW_TRY_CUDA(cudaMemcpy(d->d_shot, &d->shot, sizeof(ShotDev), cudaMemcpyHostToDevice));
     GW_TRY_CUDA(cudaStreamSynchronize(nullptr));
     return GW_OK;
@@ -938,6 +952,7 @@ gw_status gw_set_receivers(gw_domain *d, int nrec, const int *xyz)
         GW_TRY_CUDA(cudaMemset(d->d_traces, 0, tb));
     }
     d->nrec = nrec;
+    d->recs = r;
     d->shot.nrec = nrec;
     d->shot.rec = d->d_rec;
     d->shot.traces = d->d_traces;

@@ -65,6 +65,7 @@ struct gw_domain {
     long long halo_units = 0;
     // sources and receivers (host copies)
     std::vector<int4> srcs;
+    std::vector<int4> recs;               // receivers (host copy)
     std::vector<std::vector<double>> wavelets;
     int nrec = 0;
     // model
