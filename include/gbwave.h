@@ -254,7 +254,10 @@ gw_status gw_inject_source(gw_domain *d, int gx, int gy, int gz,
 gw_status gw_inject_ricker(gw_domain *d, int gx, int gy, int gz,
                            double f_peak);
 /* Receivers: nrec (x, y, z) global interior cells; trace sample n is
- * u_{n+1} at the receiver, for n < desc.nsteps.  Replaces earlier ones. */
+ * u_{n+1} at the receiver, for n < desc.nsteps.  Replaces earlier ones.
+ * GW_ERR_ARG if more than 64 sources and receivers would fall inside one
+ * work item (tile column of the domain's schedule); a batch whose items
+ * still hold more reports GW_ERR_STATE at its next synchronisation. */
 gw_status gw_set_receivers(gw_domain *d, int nrec, const int *xyz);
 
 /* Advance nsteps steps on `stream`: K-step chunks (desc.chunk) replayed

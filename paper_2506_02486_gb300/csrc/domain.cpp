@@ -81,6 +81,9 @@ gw_status fetch_err(gw_domain *d)
         return fail(GW_ERR_TIMEOUT, "a device wait gave up (error bits 0x%x)", e);
     if (e & ERRB_NONFINITE)
         return fail(GW_ERR_NUMERIC, "non-finite wavefield norm (error bits 0x%x)", e);
+    if (e & ERRB_LOCAL_OVERFLOW)
+        return fail(GW_ERR_STATE, "more than %d sources and receivers inside one work item "
+                    "(error bits 0x%x)", kMaxLocal, e);
     return fail(GW_ERR_STATE, "device error bits 0x%x", e);
 }
 
@@ -925,6 +928,25 @@ gw_status gw_inject_ricker(gw_domain *d, int gx, int gy, int gz, double f_peak)
     return add_source(d, gx, gy, gz, std::move(w));
 }
 
+// Most sources + receivers inside any one work item of the domain (the
+// kernel keeps at most kMaxLocal per item).
+static int most_per_item(const gw_domain *d, const std::vector<int4> &recs)
+{
+    int most = 0;
+    for (const Item &it : d->items) {
+        const SubDev &s = d->subs[it.sub];
+        const int x0 = s.gx0 + (it.xy & 0xffff), y0 = s.gy0 + (it.xy >> 16);
+        const int x1 = std::min(x0 + d->ti.tx, s.gx0 + s.nx), y1 = std::min(y0 + d->ti.ty, s.gy0 + s.ny);
+        const int z0 = s.gz0 + it.z0, z1 = s.gz0 + it.z1;
+        int n = 0;
+        for (const std::vector<int4> *l : {&d->srcs, &recs})
+            for (const int4 &q : *l)
+                n += q.x >= x0 && q.x < x1 && q.y >= y0 && q.y < y1 && q.z >= z0 && q.z < z1;
+        most = std::max(most, n);
+    }
+    return most;
+}
+
 gw_status gw_set_receivers(gw_domain *d, int nrec, const int *xyz)
 {
     GW_TRY(check_dom(d));
@@ -936,6 +958,12 @@ gw_status gw_set_receivers(gw_domain *d, int nrec, const int *xyz)
         if (x < 0 || y < 0 || z < 0 || x >= D.nx || y >= D.ny || z >= D.nz)
             return fail(GW_ERR_ARG, "receiver %d outside the grid", i);
         r[i] = make_int4(x, y, z, 0);
+    }
+    if (nrec > kMaxLocal - (int)d->srcs.size()) {
+        const int most = most_per_item(d, r);
+        if (most > kMaxLocal)
+            return fail(GW_ERR_ARG, "%d sources and receivers fall in one work item (at most %d); "
+                        "spread them or use a smaller zchunk", most, kMaxLocal);
     }
     std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
     GW_TRY(sync_dom(d));

@@ -14,6 +14,7 @@ import pytest
 import oracle
 import workloads
 from gpu_util import gpu_run, rel_l2, seg_for
+from paper_2506_02486_gb300 import gbwave as gw
 
 pytestmark = pytest.mark.gpu
 
@@ -209,3 +210,33 @@ def test_checkpoint_resume_is_bitwise():
             tb = s.traces(40)
     assert np.array_equal(a, b)
     assert np.array_equal(ta, tb)
+
+
+def test_tall_thin_grid_matches_oracle():
+    """Many z items over a narrow column (and a sponge only along z)."""
+    nx, ny, nz = 20, 24, 700
+    vel = workloads.layered(nx, ny, nz, seed=41)
+    src = (10, 12, 350)
+    rec = np.array([[10, 12, z] for z in range(300, 400, 7)], dtype=np.int32)
+    g = gpu_run(vel, 40, src=src, f_peak=35.0, receivers=rec, sponge=4)
+    o = oracle_for(vel, 40, src=src, f_peak=35.0, receivers=rec, sponge=4)
+    assert rel_l2(g["u"], o["u"]) <= TOL32
+    assert rel_l2(g["traces"], o["traces"]) <= TOL32
+
+
+def test_dense_receivers_in_one_tile():
+    """64 receivers in one tile column are recorded; 80 are refused up
+    front with a clear message instead of being dropped on the device."""
+    nx, ny, nz = 128, 28, 24           # two 64 x 28 tile columns
+    vel = workloads.homogeneous(nx, ny, nz)
+    src = (96, 14, 12)                 # in the other column
+    rec = np.array([[x, y, 12] for x in range(8, 24) for y in range(4, 8)],
+                   dtype=np.int32)                       # 64 cells
+    g = gpu_run(vel, 20, src=src, f_peak=40.0, receivers=rec, zchunk=nz)
+    o = oracle_for(vel, 20, src=src, f_peak=40.0, receivers=rec)
+    assert rel_l2(g["traces"], o["traces"]) <= TOL32
+    more = np.array([[x, y, 12] for x in range(8, 28) for y in range(4, 8)],
+                    dtype=np.int32)                      # 80 cells
+    with pytest.raises(gw.GWError) as e:
+        gpu_run(vel, 20, src=src, f_peak=40.0, receivers=more, zchunk=nz)
+    assert e.value.status == gw.GW_ERR_ARG and "one work item" in str(e.value)
