@@ -8,6 +8,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -253,3 +254,18 @@ def test_tile_model_prefers_fitting_tiles(lib):
             assert 1 <= gw.gw_pick_tile(dt, n, n) <= gw.gw_tile_count(dt)
     with pytest.raises(gw.GWError):
         gw.gw_pick_tile("f32", 0, 8)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No fallback: without the CUDA library the binding raises."""
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2506_02486_gb300 import gbwave as gw\n"
+            "gw.LIB_PATH = %r\n"
+            "try:\n"
+            "    gw.lib()\n"
+            "except RuntimeError as e:\n"
+            "    print('raised', 'missing' in str(e))\n" %
+            (ROOT, str(tmp_path / "absent.so")))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True,
+                         text=True, check=True).stdout
+    assert out.strip() == "raised True"
