@@ -505,6 +505,15 @@ def run_ours(args, world, rank, local, pg):
     finally:
         seg.close()
         seg1.close()
+    serving = None
+    if args.serving and args.variants:
+        # the first 200 requests of the serving stream, replayed at the same
+        # offered load: p50/p99 latency beside the throughput numbers
+        srv = run_serve(200, device=local)
+        serving = {k: srv[k] for k in (
+            "requests", "rate_per_s", "offered_load", "failed",
+            "p50_latency_s", "p99_latency_s", "aggregate_gpts", "busy_gpts",
+            "makespan_s", "max_active", "budget_bytes")}
     if rank != 0:
         return 0
     peak, peak_kind = measured_peak()
@@ -551,6 +560,7 @@ def run_ours(args, world, rank, local, pg):
         "gpu_launches": gpu_launches,
         "clocks": clocks,
         "variants": variants,
+        "serving": serving,
         "kernel_hash": kernel_hash(),
     }
     if cpu_rate is not None:
@@ -581,7 +591,7 @@ def run_serve(n=2000, *, seed=SERVE_SEED, load=SERVE_LOAD, slots=64,
     lam = load * SERVE_CAPACITY_GPTS * 1e9 / (sum(work) / len(work))
     # same draws, rescaled inter-arrival times
     arrivals = [r.arrival_s / lam for r in reqs]
-    profiles = {}
+    torch.cuda.empty_cache()          # earlier segments' blocks
     seg = Segment(budget + (8 << 30), device=device)
     try:
         srv = Server(seg, budget, max_slots=slots, chunk=chunk)
@@ -742,6 +752,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=25)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
+    ap.add_argument("--no-serving", dest="serving", action="store_false",
+                    help="skip the 200-request serving replay of the default run")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline",
                     action="store_false")
     ap.add_argument("--case", type=int, default=0,
