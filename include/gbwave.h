@@ -199,9 +199,62 @@ gw_status gw_put(gw_ctx *ctx, gw_gptr dst, int dst_rank, size_t dst_off,
 gw_status gw_get(gw_ctx *ctx, void *dst, gw_gptr src, int src_rank,
                  size_t src_off, size_t bytes, gw_stream stream);
 /* Fence (Listing 1's ompx_fence): every put/get issued through this
- * context on any stream is complete and visible to work enqueued on
- * `stream` afterwards (stream order; no host synchronisation). */
+ * context on any stream, and every non-blocking put/get below, is complete
+ * and visible to work enqueued on `stream` afterwards (stream order; no
+ * host synchronisation).  The pool streams it joins are released. */
 gw_status gw_fence(gw_ctx *ctx, gw_stream stream);
+
+/* Non-blocking one-sided put and get on the context's stream pool (section
+ * 3.2: one-sided operations run on pooled streams; "Bounded Concurrency").
+ * The copy starts after the work already enqueued on `after` (an event
+ * join; the caller's stream is not blocked) and runs on a pool stream, so
+ * it overlaps later work on `after`.  It is complete before work enqueued on
+ * a stream after gw_fence(ctx, that stream), or on the host after gw_quiet.
+ * Same range checks as gw_put / gw_get.  On a host-only context the copy is
+ * done at once.
+ *
+ * Pool policy: streams are created lazily, one per concurrent operation,
+ * and reused once released.  At most max_active (default 8) carry
+ * unreleased operations.  An operation that finds max_active streams active
+ * first makes a partial synchronisation: of the active streams whose work
+ * has completed, the oldest half (rounded up) are released and the others
+ * keep running; if none has completed, the host waits for the oldest one
+ * and releases it. */
+gw_status gw_put_nbi(gw_ctx *ctx, gw_gptr dst, int dst_rank, size_t dst_off,
+                     const void *src, size_t bytes, gw_stream after);
+gw_status gw_get_nbi(gw_ctx *ctx, void *dst, gw_gptr src, int src_rank,
+                     size_t src_off, size_t bytes, gw_stream after);
+/* Host wait for every non-blocking operation; all pool streams released. */
+gw_status gw_quiet(gw_ctx *ctx);
+/* The MAX_ACTIVE_STREAMS threshold of section 3.2: 1 .. 64.  A lower value
+ * than the current number of active streams takes effect at the next
+ * operation, which releases the oldest until the limit holds. */
+gw_status gw_set_max_active_streams(gw_ctx *ctx, int n);
+
+typedef struct gw_pool_stats {
+    int created;           /* streams created (lazily)                    */
+    int active, idle;      /* now                                          */
+    int max_active;        /* the threshold                                */
+    int peak_active;       /* most active at once                          */
+    int pad_;
+    long long ops;         /* operations issued                            */
+    long long reuses;      /* operations that reused a released stream    */
+    long long partial_syncs;  /* threshold reached                         */
+    long long released;    /* streams released by partial synchronisation  */
+    long long waited_oldest;  /* partial syncs that had to wait             */
+    long long fences;      /* fences that joined pool streams             */
+} gw_pool_stats;
+gw_status gw_pool_stats_get(gw_ctx *ctx, gw_pool_stats *out);
+
+/* The same policy on a host-side model, for tests and for sizing the
+ * threshold: nops operations are issued one per tick of a logical clock;
+ * operation i, issued at tick t, completes at tick t + duration[i]
+ * (duration >= 0).  Waiting for a stream moves the clock to its completion.
+ * stream_of_op[i] receives the pool stream each operation ran on (may be
+ * NULL); *out the counters at the end (before any final release). */
+gw_status gw_stream_pool_simulate(int max_active, int nops,
+                                  const int *duration, int *stream_of_op,
+                                  gw_pool_stats *out);
 
 /* ------------------------------------------------------------------ */
 /* domains: one shot, decomposed into px*py*pz subdomains              */

@@ -335,6 +335,11 @@ gw_status gw_ctx_create(gw_ctx **out, int device)
 gw_status gw_ctx_destroy(gw_ctx *c)
 {
     if (!c) return GW_OK;
+    if (c->device >= 0) {
+        cudaSetDevice(c->device);
+        c->pool.destroy();      // streams with pending work finish first
+        for (cudaEvent_t ev : c->pool_events) cudaEventDestroy(ev);
+    }
     delete c;
     return GW_OK;
 }
@@ -490,6 +495,92 @@ gw_status gw_fence(gw_ctx *c, gw_stream stream)
         if (e != cudaSuccess) return cuda_fail(e, "fence join");
     }
     c->put_streams.clear();
+    // and every pool stream with an unreleased operation; joined streams are
+    // released (work issued on them later is ordered after the join anyway)
+    const std::vector<int> &act = c->pool.active();
+    for (int idx : act) {
+        cudaEvent_t ev = c->pool_events[idx];
+        GW_TRY_CUDA(cudaEventRecord(ev, c->pool.handle(idx)));
+        GW_TRY_CUDA(cudaStreamWaitEvent(target, ev, 0));
+    }
+    if (!act.empty()) c->pool.count_fence();
+    c->pool.release_all();
+    return GW_OK;
+}
+
+// One copy on a pool stream, after the work already on `after`.
+static gw_status pool_copy(gw_ctx *c, void *dst, const void *src, size_t bytes,
+                           cudaStream_t after)
+{
+    GW_TRY_CUDA(cudaSetDevice(c->device));
+    int idx = -1;
+    GW_TRY(c->pool.acquire(&idx));
+    while ((int)c->pool_events.size() <= idx) {
+        cudaEvent_t ev;
+        GW_TRY_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        c->pool_events.push_back(ev);
+    }
+    cudaStream_t ps = c->pool.handle(idx);
+    cudaEvent_t ev = c->pool_events[idx];
+    GW_TRY_CUDA(cudaEventRecord(ev, after));
+    GW_TRY_CUDA(cudaStreamWaitEvent(ps, ev, 0));
+    GW_TRY_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ps));
+    return GW_OK;
+}
+
+gw_status gw_put_nbi(gw_ctx *c, gw_gptr dst, int dst_rank, size_t dst_off,
+                     const void *src, size_t bytes, gw_stream after)
+{
+    if (!c || (!src && bytes)) return fail(GW_ERR_ARG, "NULL argument");
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    char *p = nullptr;
+    GW_TRY(remote_copy(c, dst, dst_rank, dst_off, bytes, &p));
+    if (!bytes) return GW_OK;
+    if (c->device < 0) {
+        std::memcpy(p, src, bytes);
+        return GW_OK;
+    }
+    return pool_copy(c, p, src, bytes, static_cast<cudaStream_t>(after));
+}
+
+gw_status gw_get_nbi(gw_ctx *c, void *dst, gw_gptr src, int src_rank,
+                     size_t src_off, size_t bytes, gw_stream after)
+{
+    if (!c || (!dst && bytes)) return fail(GW_ERR_ARG, "NULL argument");
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    char *p = nullptr;
+    GW_TRY(remote_copy(c, src, src_rank, src_off, bytes, &p));
+    if (!bytes) return GW_OK;
+    if (c->device < 0) {
+        std::memcpy(dst, p, bytes);
+        return GW_OK;
+    }
+    return pool_copy(c, dst, p, bytes, static_cast<cudaStream_t>(after));
+}
+
+gw_status gw_quiet(gw_ctx *c)
+{
+    if (!c) return fail(GW_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    if (c->device < 0) return GW_OK;
+    GW_TRY_CUDA(cudaSetDevice(c->device));
+    return c->pool.quiet();
+}
+
+gw_status gw_set_max_active_streams(gw_ctx *c, int n)
+{
+    if (!c) return fail(GW_ERR_ARG, "ctx is NULL");
+    if (n < 1 || n > 64) return fail(GW_ERR_ARG, "max active streams must be 1 .. 64, got %d", n);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    c->pool.set_max_active(n);
+    return GW_OK;
+}
+
+gw_status gw_pool_stats_get(gw_ctx *c, gw_pool_stats *out)
+{
+    if (!c || !out) return fail(GW_ERR_ARG, "NULL argument");
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    *out = c->pool.stats();
     return GW_OK;
 }
 

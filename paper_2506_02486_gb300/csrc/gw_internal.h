@@ -13,6 +13,7 @@
 #include "gbwave.h"
 #include "gw_device.h"
 #include "gw_kernels.h"
+#include "stream_pool.h"
 
 namespace gw {
 
@@ -34,6 +35,34 @@ gw_status cuda_fail(cudaError_t e, const char *what);
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// CUDA streams for the stream pool: non-blocking (no implicit order with the
+// legacy default stream), created on the context's device.
+struct CudaStreams {
+    using Handle = cudaStream_t;
+    gw_status create(Handle *h)
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(h, cudaStreamNonBlocking);
+        return e == cudaSuccess ? GW_OK : cuda_fail(e, "pool stream create");
+    }
+    gw_status done(Handle h, bool *d)
+    {
+        cudaError_t e = cudaStreamQuery(h);
+        if (e == cudaErrorNotReady) {
+            (void)cudaGetLastError();   // not an error: still running
+            *d = false;
+            return GW_OK;
+        }
+        *d = e == cudaSuccess;
+        return e == cudaSuccess ? GW_OK : cuda_fail(e, "pool stream query");
+    }
+    gw_status sync(Handle h)
+    {
+        cudaError_t e = cudaStreamSynchronize(h);
+        return e == cudaSuccess ? GW_OK : cuda_fail(e, "pool stream sync");
+    }
+    void destroy(Handle h) { cudaStreamDestroy(h); }
+};
 
 // One global allocation (paper section 3.2).
 struct Alloc {
@@ -85,6 +114,9 @@ struct gw_ctx {
     uint64_t cache_hits = 0, cache_misses = 0;
     // streams that carried puts since the last fence
     std::vector<cudaStream_t> put_streams;
+    // streams of the non-blocking puts and gets (bounded concurrency)
+    gw::StreamPool<gw::CudaStreams> pool;
+    std::vector<cudaEvent_t> pool_events;   // one per pool stream (joins)
     std::recursive_mutex mu;
     int num_sms = 0;
     // autotuner results: shape/split/type key -> time per step of each tile

@@ -102,6 +102,17 @@ class gw_server_stats(ctypes.Structure):
     ]
 
 
+class gw_pool_stats(ctypes.Structure):
+    _fields_ = [
+        ("created", ctypes.c_int), ("active", ctypes.c_int),
+        ("idle", ctypes.c_int), ("max_active", ctypes.c_int),
+        ("peak_active", ctypes.c_int), ("pad_", ctypes.c_int),
+        ("ops", ctypes.c_longlong), ("reuses", ctypes.c_longlong),
+        ("partial_syncs", ctypes.c_longlong), ("released", ctypes.c_longlong),
+        ("waited_oldest", ctypes.c_longlong), ("fences", ctypes.c_longlong),
+    ]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _SZ = ctypes.c_size_t
@@ -126,6 +137,12 @@ _SIGS = {
     "gw_put": [_P, _U64, _I, _SZ, _P, _SZ, _P],
     "gw_get": [_P, _P, _U64, _I, _SZ, _SZ, _P],
     "gw_fence": [_P, _P],
+    "gw_put_nbi": [_P, _U64, _I, _SZ, _P, _SZ, _P],
+    "gw_get_nbi": [_P, _P, _U64, _I, _SZ, _SZ, _P],
+    "gw_quiet": [_P],
+    "gw_set_max_active_streams": [_P, _I],
+    "gw_pool_stats_get": [_P, ctypes.POINTER(gw_pool_stats)],
+    "gw_stream_pool_simulate": [_I, _I, _P, _P, ctypes.POINTER(gw_pool_stats)],
     "gw_domain_create": [_P, ctypes.POINTER(gw_shot_desc), _I, _I, _I, _P,
                          _P, _P, _I, ctypes.POINTER(_P)],
     "gw_domain_destroy": [_P],
@@ -322,6 +339,52 @@ def gw_get(ctx: int, dst, src: int, src_rank: int, src_off: int,
 
 def gw_fence(ctx: int, stream=None):
     _check(lib().gw_fence(ctx, _stream(stream)), "gw_fence")
+
+
+def gw_put_nbi(ctx: int, dst: int, dst_rank: int, dst_off: int, src,
+               nbytes: int, after=None):
+    _check(lib().gw_put_nbi(ctx, int(dst), int(dst_rank), int(dst_off),
+                            _ptr(src), int(nbytes), _stream(after)),
+           "gw_put_nbi")
+
+
+def gw_get_nbi(ctx: int, dst, src: int, src_rank: int, src_off: int,
+               nbytes: int, after=None):
+    _check(lib().gw_get_nbi(ctx, _ptr(dst), int(src), int(src_rank),
+                            int(src_off), int(nbytes), _stream(after)),
+           "gw_get_nbi")
+
+
+def gw_quiet(ctx: int):
+    _check(lib().gw_quiet(ctx), "gw_quiet")
+
+
+def gw_set_max_active_streams(ctx: int, n: int):
+    _check(lib().gw_set_max_active_streams(ctx, int(n)),
+           "gw_set_max_active_streams")
+
+
+def _pool_dict(s: gw_pool_stats) -> dict:
+    return {k: getattr(s, k) for k, _ in gw_pool_stats._fields_
+            if k != "pad_"}
+
+
+def gw_pool_stats_get(ctx: int) -> dict:
+    s = gw_pool_stats()
+    _check(lib().gw_pool_stats_get(ctx, ctypes.byref(s)), "gw_pool_stats_get")
+    return _pool_dict(s)
+
+
+def gw_stream_pool_simulate(max_active: int, durations):
+    """The pool policy on the host model; returns (stream of each op,
+    counters)."""
+    d = np.ascontiguousarray(durations, dtype=np.int32)
+    so = np.full(d.shape[0], -1, dtype=np.int32)
+    s = gw_pool_stats()
+    _check(lib().gw_stream_pool_simulate(int(max_active), int(d.shape[0]),
+                                         _ptr(d), _ptr(so), ctypes.byref(s)),
+           "gw_stream_pool_simulate")
+    return so, _pool_dict(s)
 
 
 # ---------------------------------------------------------------- domains
