@@ -257,6 +257,48 @@ gw_status gw_stream_pool_simulate(int max_active, int nops,
                                   gw_pool_stats *out);
 
 /* ------------------------------------------------------------------ */
+/* Cannon's ring exchange (section 5, matrix multiplication): C = A B    */
+/* over P ranks of one segment, BF16 operands, FP32 accumulation on the  */
+/* tensor cores.                                                         */
+
+typedef struct gw_cannon gw_cannon;
+
+/* Segment bytes each rank needs for an N x N product over P ranks (its A
+ * stripe, two B stripe buffers, its C stripe).  GW_ERR_ARG unless
+ * 1 <= P <= 64 and N is a positive multiple of P. */
+gw_status gw_cannon_bytes(int n, int p, size_t *per_rank);
+/* A ring of P ranks (ranks 0 .. P-1 of the context's segment, which needs
+ * at least P ranks of gw_cannon_bytes each).  Stripe width Ns = N / P; rank
+ * r owns rows r Ns .. r Ns + Ns - 1 of A and of C.  N must be a multiple of
+ * 8 (GW_ERR_ALIGN).  Needs a device context (GW_ERR_STATE). */
+gw_status gw_cannon_create(gw_ctx *ctx, int n, int p, gw_cannon **out);
+gw_status gw_cannon_destroy(gw_cannon *cn);
+/* Load the operands: a = A and bt = B^T (that is, B in column-major order),
+ * both N x N row-major arrays of BF16 bit patterns (uint16), on the host
+ * (on_device = 0) or the device.  Rank r receives A's row stripe r and B's
+ * column stripe r.  Synchronous. */
+gw_status gw_cannon_set(gw_cannon *cn, const void *a, const void *bt,
+                        int on_device);
+/* The P steps of the ring, enqueued on `stream`: in step s rank r
+ * multiplies its A stripe by the B column stripe it holds, writing one
+ * Ns x Ns block of its C stripe, while non-blocking puts (stream pool) send
+ * that stripe to rank r - 1's spare buffer; a fence orders step s + 1 after
+ * them.  Runs may be repeated (the stripes keep travelling; each run writes
+ * all of C).  Device waits are bounded: a kernel that gave up is reported as
+ * GW_ERR_TIMEOUT by gw_cannon_sync / gw_cannon_read_c. */
+gw_status gw_cannon_run(gw_cannon *cn, gw_stream stream);
+/* Device synchronisation and the kernel error word. */
+gw_status gw_cannon_sync(gw_cannon *cn);
+/* C (N x N, row-major FP32) to the host (on_device = 0) or the device,
+ * after a device synchronisation. */
+gw_status gw_cannon_read_c(gw_cannon *cn, void *out, int on_device);
+/* Per-launch CUDA-event timing of the block-product kernel (synchronises
+ * after each launch while enabled; resets the counters). */
+gw_status gw_cannon_timing(gw_cannon *cn, int enable);
+gw_status gw_cannon_stats(gw_cannon *cn, double *gemm_ms, long long *launches,
+                          int *grid);
+
+/* ------------------------------------------------------------------ */
 /* domains: one shot, decomposed into px*py*pz subdomains              */
 
 /* Create a shot domain decomposed into px x py x pz subdomains (subdomain

@@ -1,0 +1,269 @@
+// gemm_tc.cu -- the block products of Cannon's ring steps (section 5, matrix
+// multiplication): C_q = A_q * B_q^T for a set of problems q, BF16 operands,
+// FP32 accumulation, on the 5th-generation tensor cores.
+//
+// One persistent CTA per SM, six warps:
+//   warp 0      TMA producer: 128 x 64 A and 256 x 64 B tiles (K-major,
+//               128-byte swizzle) into a 4-stage shared-memory ring;
+//   warp 1      allocates 512 tensor-memory columns (two 128 x 256 FP32
+//               accumulators) and issues tcgen05.mma (M 128, N 256, K 16);
+//   warps 2-5   epilogue: tensor memory -> registers -> C, while the MMA
+//               warp fills the other accumulator.
+// Every wait is bounded; a wait that gives up latches ERRB_TIMEOUT, the CTA
+// drains what it has in flight (bounded), frees its tensor memory and leaves.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "gw_kernels.h"
+#include "tc_ptx.cuh"
+
+namespace gw {
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4, GROUP_M = 8;
+constexpr int A_BYTES = BM * BK * 2;            // 16 KB
+constexpr int B_BYTES = BN * BK * 2;            // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int THREADS = 192;
+constexpr uint32_t TMEM_COLS = 2 * BN;          // two accumulators
+// barriers: full[S], empty[S], tfull[2], tempty[2], drain; then the TMEM
+// base address and an abort flag
+constexpr int OFF_BAR = STAGES * STAGE_BYTES;
+constexpr int NBAR = 2 * STAGES + 5;
+constexpr int OFF_TMEM = OFF_BAR + 8 * NBAR;
+constexpr int SMEM_USED = OFF_TMEM + 16;
+constexpr int SMEM_BYTES = SMEM_USED + 1024;    // + alignment of the ring
+
+struct TileCoord {
+    int q, tm, tn;
+};
+
+// Tile t of the launch: problems one after another; inside a problem,
+// groups of GROUP_M tile rows swept column by column, so the CTAs running
+// at the same time share A rows and B columns in L2.
+__device__ __forceinline__ TileCoord tile_of(int t, int tmc, int tnc)
+{
+    const int per = tmc * tnc;
+    TileCoord c;
+    c.q = t / per;
+    const int u = t - c.q * per;
+    const int g = u / (GROUP_M * tnc);
+    const int first = g * GROUP_M;
+    const int gs = min(GROUP_M, tmc - first);
+    const int v = u - g * GROUP_M * tnc;
+    c.tm = first + v % gs;
+    c.tn = v / gs;
+    return c;
+}
+
+__device__ __forceinline__ bool bwait(uint64_t *bar, uint32_t parity, volatile int *abortf)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_timer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63u) == 0) {
+            if (*abortf) return false;
+            if (global_timer() - t0 > kWaitLimitNs) return false;
+        }
+    }
+}
+
+// The same bound without the abort shortcut: draining copies and MMAs that
+// are already in flight must not be cut short by another warp giving up.
+__device__ __forceinline__ bool bwait_drain(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_timer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63u) == 0 && global_timer() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void give_up(volatile int *abortf, unsigned *err)
+{
+    if (!*abortf) atomicOr(err, ERRB_TIMEOUT);
+    *abortf = 1;
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
+            const __grid_constant__ CUtensorMap map_b,
+            const __grid_constant__ GemmArgs A)
+{
+    extern __shared__ unsigned char smem_raw[];
+    // 1024-byte alignment: the swizzle pattern repeats every 8 rows of 128 B
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
+    uint64_t *full = bars, *empty = bars + STAGES;
+    uint64_t *tfull = bars + 2 * STAGES, *tempty = tfull + 2, *drain = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + OFF_TMEM);
+    volatile int *abortf = reinterpret_cast<volatile int *>(smem + OFF_TMEM + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tmc = (A.m + BM - 1) / BM, tnc = (A.n + BN - 1) / BN;
+    const int ntiles = A.nprob * tmc * tnc;
+    const int nkb = (A.k + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);        // one arrival per epilogue warp
+        }
+        mbar_init(drain, 1);
+        *abortf = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            const uint64_t pol = policy_evict_normal();
+            uint32_t it = 0;
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                const TileCoord tc_ = tile_of(t, tmc, tnc);
+                const int ra = A.a_rank[tc_.q], rb = A.b_rank[tc_.q];
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const uint32_t s = it % STAGES;
+                    if (it >= STAGES &&
+                        !bwait(&empty[s], ((it / STAGES) - 1) & 1u, abortf)) {
+                        give_up(abortf, A.err);
+                        goto produced;
+                    }
+                    unsigned char *st = smem + s * STAGE_BYTES;
+                    mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_3d(st, &map_a, &full[s], kb * BK, tc_.tm * BM, ra, pol);
+                    tma_load_3d(st + A_BYTES, &map_b, &full[s], kb * BK, tc_.tn * BN, rb, pol);
+                }
+            }
+        produced:
+            // leave only after the copies issued into shared memory landed
+            for (uint32_t q = it > STAGES ? it - STAGES : 0; q < it; ++q)
+                if (!bwait_drain(&full[q % STAGES], (q / STAGES) & 1u)) break;
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+            uint32_t it = 0, local = 0;
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+                const uint32_t b = local & 1u;
+                if (local >= 2 && !bwait(&tempty[b], ((local >> 1) - 1) & 1u, abortf)) {
+                    give_up(abortf, A.err);
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t d = tmem + b * BN;
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const uint32_t s = it % STAGES;
+                    if (!bwait(&full[s], (it / STAGES) & 1u, abortf)) {
+                        give_up(abortf, A.err);
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const unsigned char *st = smem + s * STAGE_BYTES;
+                    const uint64_t ad = tc::sdesc_k128(st);
+                    const uint64_t bd = tc::sdesc_k128(st + A_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk)   // 32 bytes along K each
+                        tc::mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc,
+                                     (kb | kk) != 0);
+                    tc::commit(&empty[s]);                 // stage free when done
+                }
+                if (!ok) break;
+                tc::commit(&tfull[b]);                     // accumulator ready
+            }
+            // no MMA may still be running when the CTA leaves
+            tc::commit(drain);
+            bwait_drain(drain, 0);
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int lg = warp & 3;                  // TMEM lane group of this warp
+        const int row_in_tile = 32 * lg + lane;
+        uint32_t local = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+            const uint32_t b = local & 1u;
+            if (!bwait(&tfull[b], (local >> 1) & 1u, abortf)) {
+                give_up(abortf, A.err);
+                break;
+            }
+            tc::fence_after_sync();
+            const TileCoord tc_ = tile_of(t, tmc, tnc);
+            const int row = tc_.tm * BM + row_in_tile;
+            const int col0 = tc_.tn * BN;
+            float *crow = A.c + A.c_off[tc_.q] + (long long)row * A.ldc + col0;
+            const bool vec = ((reinterpret_cast<uintptr_t>(crow) & 15u) == 0);
+#pragma unroll 1
+            for (int ch = 0; ch < BN / 32; ++ch) {
+                float v[32];
+                tc::ld_32cols(tmem + ((uint32_t)(32 * lg) << 16) + b * BN + ch * 32, v);
+                if (row >= A.m) continue;
+                const int c0 = col0 + ch * 32;
+                float *p = crow + ch * 32;
+                if (vec && c0 + 32 <= A.n) {
+#pragma unroll
+                    for (int i = 0; i < 32; i += 4)
+                        *reinterpret_cast<float4 *>(p + i) =
+                            make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (c0 + i < A.n) p[i] = v[i];
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+    }
+
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tmem, TMEM_COLS);
+}
+
+}  // namespace
+
+int gemm_smem_bytes() { return SMEM_BYTES; }
+int gemm_tile_m() { return BM; }
+int gemm_tile_n() { return BN; }
+
+cudaError_t launch_gemm_bf16(const void *map_a, const void *map_b, const GemmArgs &a,
+                             int grid, cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    CUtensorMap ma, mb;
+    memcpy(&ma, map_a, sizeof ma);
+    memcpy(&mb, map_b, sizeof mb);
+    k_gemm_bf16<<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, a);
+    return cudaGetLastError();
+}
+
+}  // namespace gw

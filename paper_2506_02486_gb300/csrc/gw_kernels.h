@@ -106,4 +106,28 @@ cudaError_t launch_check(const SubDev &sub, int cur, int dtype,
 cudaError_t launch_check_sum(const double *part, int nplanes, double *out,
                              cudaStream_t s);
 
+// ---- tensor-core block products (gemm_tc.cu) ----
+
+// C_q = A_q B_q^T for up to kGemmMaxProb problems of one shape: A_q is an
+// m x k BF16 stripe and B_q an n x k BF16 stripe (both K contiguous), read
+// through 3-D tensor maps {k, rows, rank} (128-byte swizzle; boxes 64 x 128
+// for A, 64 x 256 for B); C_q is m x n FP32 at c + c_off[q], row pitch ldc.
+constexpr int kGemmMaxProb = 64;
+struct GemmArgs {
+    int nprob;
+    int k, m, n;
+    int a_rank[kGemmMaxProb];       // rank coordinate of problem q's A stripe
+    int b_rank[kGemmMaxProb];       // rank coordinate of its B stripe
+    long long c_off[kGemmMaxProb];  // element offset of its block in c
+    float *c;
+    long long ldc;
+    unsigned *err;                  // ERRB_TIMEOUT when a wait gave up
+};
+int gemm_smem_bytes();
+int gemm_tile_m();
+int gemm_tile_n();
+// map_a / map_b: host copies of the encoded tensor maps (CUtensorMap).
+cudaError_t launch_gemm_bf16(const void *map_a, const void *map_b, const GemmArgs &a,
+                             int grid, cudaStream_t s);
+
 }  // namespace gw

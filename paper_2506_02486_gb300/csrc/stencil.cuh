@@ -211,12 +211,6 @@ __device__ __forceinline__ bool wait_slot(uint64_t *bar, uint32_t parity,
     }
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];"
-                 :: "r"(smem_addr(bar)) : "memory");
-}
-
 // Barrier among the consumer warps only (the producer warp is not part).
 __device__ __forceinline__ void consumer_sync(int nthreads)
 {

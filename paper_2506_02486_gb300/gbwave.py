@@ -143,6 +143,16 @@ _SIGS = {
     "gw_set_max_active_streams": [_P, _I],
     "gw_pool_stats_get": [_P, ctypes.POINTER(gw_pool_stats)],
     "gw_stream_pool_simulate": [_I, _I, _P, _P, ctypes.POINTER(gw_pool_stats)],
+    "gw_cannon_bytes": [_I, _I, ctypes.POINTER(_SZ)],
+    "gw_cannon_create": [_P, _I, _I, ctypes.POINTER(_P)],
+    "gw_cannon_destroy": [_P],
+    "gw_cannon_set": [_P, _P, _P, _I],
+    "gw_cannon_run": [_P, _P],
+    "gw_cannon_sync": [_P],
+    "gw_cannon_read_c": [_P, _P, _I],
+    "gw_cannon_timing": [_P, _I],
+    "gw_cannon_stats": [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
+                        ctypes.POINTER(_I)],
     "gw_domain_create": [_P, ctypes.POINTER(gw_shot_desc), _I, _I, _I, _P,
                          _P, _P, _I, ctypes.POINTER(_P)],
     "gw_domain_destroy": [_P],
@@ -385,6 +395,56 @@ def gw_stream_pool_simulate(max_active: int, durations):
                                          _ptr(d), _ptr(so), ctypes.byref(s)),
            "gw_stream_pool_simulate")
     return so, _pool_dict(s)
+
+
+# ---------------------------------------------------------------- Cannon
+
+def gw_cannon_bytes(n: int, p: int) -> int:
+    v = _SZ()
+    _check(lib().gw_cannon_bytes(int(n), int(p), ctypes.byref(v)),
+           "gw_cannon_bytes")
+    return v.value
+
+
+def gw_cannon_create(ctx: int, n: int, p: int) -> int:
+    h = _P()
+    _check(lib().gw_cannon_create(ctx, int(n), int(p), ctypes.byref(h)),
+           "gw_cannon_create")
+    return h.value
+
+
+def gw_cannon_destroy(cn: int):
+    _check(lib().gw_cannon_destroy(cn), "gw_cannon_destroy")
+
+
+def gw_cannon_set(cn: int, a, bt, on_device: bool = False):
+    _check(lib().gw_cannon_set(cn, _ptr(a), _ptr(bt), int(bool(on_device))),
+           "gw_cannon_set")
+
+
+def gw_cannon_run(cn: int, stream=None):
+    _check(lib().gw_cannon_run(cn, _stream(stream)), "gw_cannon_run")
+
+
+def gw_cannon_sync(cn: int):
+    _check(lib().gw_cannon_sync(cn), "gw_cannon_sync")
+
+
+def gw_cannon_read_c(cn: int, out, on_device: bool = False):
+    _check(lib().gw_cannon_read_c(cn, _ptr(out), int(bool(on_device))),
+           "gw_cannon_read_c")
+    return out
+
+
+def gw_cannon_timing(cn: int, enable: bool):
+    _check(lib().gw_cannon_timing(cn, int(bool(enable))), "gw_cannon_timing")
+
+
+def gw_cannon_stats(cn: int) -> dict:
+    ms, n, g = _D(), ctypes.c_longlong(), _I()
+    _check(lib().gw_cannon_stats(cn, ctypes.byref(ms), ctypes.byref(n),
+                                 ctypes.byref(g)), "gw_cannon_stats")
+    return {"gemm_ms": ms.value, "launches": n.value, "grid": g.value}
 
 
 # ---------------------------------------------------------------- domains
