@@ -26,7 +26,8 @@ struct gw_cannon {
     gw_gptr ga = 0, gb[2] = {0, 0}, gc = 0;
     int cur = 0;              // B buffer holding the current stripes
     int off = 0;              // rank r holds B column stripe (r + off) mod p
-    CUtensorMap map_a, map_b[2];
+    CUtensorMap map_a, map_b[2][2];   // [buffer][cluster size - 1]
+    int cluster = 2;          // CTAs sharing one B tile (TMA multicast)
     unsigned *err = nullptr;  // device error word
     gw_gptr gerr = 0;
     bool timing = false;
@@ -115,7 +116,8 @@ gw_status launch_step(gw_cannon *cn, cudaStream_t s)
     a.ldc = cn->n;
     a.err = cn->err;
     if (cn->timing) GW_TRY_CUDA(cudaEventRecord(cn->ev0, s));
-    GW_TRY_CUDA(launch_gemm_bf16(&cn->map_a, &cn->map_b[cn->cur], a, cn->grid, s));
+    GW_TRY_CUDA(launch_gemm_bf16(&cn->map_a, &cn->map_b[cn->cur][cn->cluster - 1], a,
+                                 cn->cluster, cn->grid, s));
     if (cn->timing) {
         GW_TRY_CUDA(cudaEventRecord(cn->ev1, s));
         GW_TRY_CUDA(cudaEventSynchronize(cn->ev1));
@@ -124,6 +126,20 @@ gw_status launch_step(gw_cannon *cn, cudaStream_t s)
         cn->gemm_ms += ms;
     }
     ++cn->launches;
+    return GW_OK;
+}
+
+// One resident CTA per SM (a multiple of the cluster size), never more CTAs
+// than tiles.
+gw_status set_grid(gw_cannon *cn, int cluster)
+{
+    const int tm = (cn->ns + gemm_tile_m() - 1) / gemm_tile_m();
+    const int tn = (cn->ns + gemm_tile_n() - 1) / gemm_tile_n();
+    const int units = cn->p * ((tm + cluster - 1) / cluster) * tn;
+    const int most = gemm_max_ctas(cluster, cn->ctx->num_sms);
+    if (most < cluster) return fail(GW_ERR_CUDA, "no resident cluster of %d CTAs", cluster);
+    cn->cluster = cluster;
+    cn->grid = std::min(most, units * cluster);
     return GW_OK;
 }
 
@@ -182,17 +198,25 @@ gw_status gw_cannon_create(gw_ctx *c, int n, int p, gw_cannon **out)
     if (cudaMemset(cn->err, 0, sizeof(unsigned)) != cudaSuccess)
         return cleanup(fail(GW_ERR_CUDA, "error word"));
     st = encode_stripes(cn, &cn->map_a, cn->ga, gemm_tile_m());
-    if (st == GW_OK) st = encode_stripes(cn, &cn->map_b[0], cn->gb[0], gemm_tile_n());
-    if (st == GW_OK) st = encode_stripes(cn, &cn->map_b[1], cn->gb[1], gemm_tile_n());
+    for (int b = 0; b < 2 && st == GW_OK; ++b)
+        for (int cl = 1; cl <= 2 && st == GW_OK; ++cl)
+            st = encode_stripes(cn, &cn->map_b[b][cl - 1], cn->gb[b], gemm_tile_n() / cl);
     if (st != GW_OK) return cleanup(st);
     if (cudaEventCreate(&cn->ev0) != cudaSuccess || cudaEventCreate(&cn->ev1) != cudaSuccess)
         return cleanup(fail(GW_ERR_CUDA, "events"));
-    // one CTA per SM, never more CTAs than tiles
-    const int tiles = p * ((cn->ns + gemm_tile_m() - 1) / gemm_tile_m()) *
-                      ((cn->ns + gemm_tile_n() - 1) / gemm_tile_n());
-    cn->grid = std::max(1, std::min(c->num_sms, tiles));
+    st = set_grid(cn, 2);
+    if (st != GW_OK) return cleanup(st);
     *out = cn;
     return GW_OK;
+}
+
+gw_status gw_cannon_set_cluster(gw_cannon *cn, int cluster)
+{
+    if (!cn) return fail(GW_ERR_ARG, "NULL argument");
+    if (cluster != 1 && cluster != 2) return fail(GW_ERR_ARG, "cluster size must be 1 or 2");
+    std::lock_guard<std::recursive_mutex> lk(cn->ctx->mu);
+    GW_TRY_CUDA(cudaSetDevice(cn->ctx->device));
+    return set_grid(cn, cluster);
 }
 
 gw_status gw_cannon_destroy(gw_cannon *cn)

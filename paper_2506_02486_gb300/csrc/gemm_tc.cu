@@ -43,16 +43,16 @@ struct TileCoord {
 // Tile t of the launch: problems one after another; inside a problem,
 // groups of GROUP_M tile rows swept column by column, so the CTAs running
 // at the same time share A rows and B columns in L2.
-__device__ __forceinline__ TileCoord tile_of(int t, int tmc, int tnc)
+__device__ __forceinline__ TileCoord tile_of(int t, int tmc, int tnc, int group)
 {
     const int per = tmc * tnc;
     TileCoord c;
     c.q = t / per;
     const int u = t - c.q * per;
-    const int g = u / (GROUP_M * tnc);
-    const int first = g * GROUP_M;
-    const int gs = min(GROUP_M, tmc - first);
-    const int v = u - g * GROUP_M * tnc;
+    const int g = u / (group * tnc);
+    const int first = g * group;
+    const int gs = min(group, tmc - first);
+    const int v = u - g * group * tnc;
     c.tm = first + v % gs;
     c.tn = v / gs;
     return c;
@@ -89,6 +89,13 @@ __device__ __forceinline__ void give_up(volatile int *abortf, unsigned *err)
     *abortf = 1;
 }
 
+// CL = 1: one CTA per tile.  CL = 2: a cluster of two CTAs on vertically
+// adjacent tiles (tile rows 2i and 2i + 1, same tile column); each loads its
+// own A tile and one half of the shared B tile, multicast into both CTAs,
+// so a CTA fetches 32 KB from L2 per K step instead of 48 KB.  A stage may
+// then only be refilled once both CTAs' MMAs are done with it: each MMA
+// warp's commit arrives on the empty barrier of both CTAs (count 2).
+template <int CL>
 __global__ void __launch_bounds__(THREADS, 1)
 k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
             const __grid_constant__ CUtensorMap map_b,
@@ -96,6 +103,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
 {
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte alignment: the swizzle pattern repeats every 8 rows of 128 B
+    // (the same offset in every CTA, as multicast requires)
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
@@ -105,14 +113,19 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
     volatile int *abortf = reinterpret_cast<volatile int *>(smem + OFF_TMEM + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int crank = CL > 1 ? (int)tc::cluster_ctarank() : 0;
+    const int unit0 = CL > 1 ? (int)tc::cluster_id_x() : (int)blockIdx.x;
+    const int nunit_step = CL > 1 ? (int)tc::ncluster_x() : (int)gridDim.x;
     const int tmc = (A.m + BM - 1) / BM, tnc = (A.n + BN - 1) / BN;
-    const int ntiles = A.nprob * tmc * tnc;
+    const int tmu = (tmc + CL - 1) / CL;          // tile-row units
+    const int nunits = A.nprob * tmu * tnc;
     const int nkb = (A.k + BK - 1) / BK;
+    constexpr uint16_t kPeers = (uint16_t)((1u << CL) - 1u);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], CL);        // one commit per CTA of the cluster
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
@@ -128,6 +141,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
     }
     tc::fence_before_sync();
     __syncthreads();
+    if (CL > 1) tc::cluster_sync();          // peers' barriers exist
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
@@ -136,8 +150,9 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
         if (lane == 0) {
             const uint64_t pol = policy_evict_normal();
             uint32_t it = 0;
-            for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-                const TileCoord tc_ = tile_of(t, tmc, tnc);
+            for (int u = unit0; u < nunits; u += nunit_step) {
+                const TileCoord tc_ = tile_of(u, tmu, tnc, GROUP_M / CL);
+                const int tm = tc_.tm * CL + crank;
                 const int ra = A.a_rank[tc_.q], rb = A.b_rank[tc_.q];
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const uint32_t s = it % STAGES;
@@ -148,8 +163,14 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
                     }
                     unsigned char *st = smem + s * STAGE_BYTES;
                     mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                    tma_load_3d(st, &map_a, &full[s], kb * BK, tc_.tm * BM, ra, pol);
-                    tma_load_3d(st + A_BYTES, &map_b, &full[s], kb * BK, tc_.tn * BN, rb, pol);
+                    tma_load_3d(st, &map_a, &full[s], kb * BK, tm * BM, ra, pol);
+                    if (CL == 1)
+                        tma_load_3d(st + A_BYTES, &map_b, &full[s], kb * BK, tc_.tn * BN,
+                                    rb, pol);
+                    else
+                        tc::tma_load_3d_mc(st + A_BYTES + crank * (B_BYTES / CL), &map_b,
+                                           &full[s], kb * BK,
+                                           tc_.tn * BN + crank * (BN / CL), rb, kPeers, pol);
                 }
             }
         produced:
@@ -162,7 +183,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
             uint32_t it = 0, local = 0;
-            for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+            for (int u = unit0; u < nunits; u += nunit_step, ++local) {
                 const uint32_t b = local & 1u;
                 if (local >= 2 && !bwait(&tempty[b], ((local >> 1) - 1) & 1u, abortf)) {
                     give_up(abortf, A.err);
@@ -186,7 +207,9 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
                     for (int kk = 0; kk < BK / 16; ++kk)   // 32 bytes along K each
                         tc::mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc,
                                      (kb | kk) != 0);
-                    tc::commit(&empty[s]);                 // stage free when done
+                    // stage free (in every CTA that wrote into it) when done
+                    if (CL == 1) tc::commit(&empty[s]);
+                    else tc::commit_mc(&empty[s], kPeers);
                 }
                 if (!ok) break;
                 tc::commit(&tfull[b]);                     // accumulator ready
@@ -200,15 +223,15 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
         const int lg = warp & 3;                  // TMEM lane group of this warp
         const int row_in_tile = 32 * lg + lane;
         uint32_t local = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+        for (int u = unit0; u < nunits; u += nunit_step, ++local) {
             const uint32_t b = local & 1u;
             if (!bwait(&tfull[b], (local >> 1) & 1u, abortf)) {
                 give_up(abortf, A.err);
                 break;
             }
             tc::fence_after_sync();
-            const TileCoord tc_ = tile_of(t, tmc, tnc);
-            const int row = tc_.tm * BM + row_in_tile;
+            const TileCoord tc_ = tile_of(u, tmu, tnc, GROUP_M / CL);
+            const int row = (tc_.tm * CL + crank) * BM + row_in_tile;
             const int col0 = tc_.tn * BN;
             float *crow = A.c + A.c_off[tc_.q] + (long long)row * A.ldc + col0;
             const bool vec = ((reinterpret_cast<uintptr_t>(crow) & 15u) == 0);
@@ -238,6 +261,9 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
 
     tc::fence_before_sync();
     __syncthreads();
+    // a peer may still multicast into this CTA or arrive on its barriers
+    // until it has drained its own copies and MMAs
+    if (CL > 1) tc::cluster_sync();
     tc::fence_after_sync();
     if (warp == 1) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
@@ -248,22 +274,69 @@ int gemm_smem_bytes() { return SMEM_BYTES; }
 int gemm_tile_m() { return BM; }
 int gemm_tile_n() { return BN; }
 
-cudaError_t launch_gemm_bf16(const void *map_a, const void *map_b, const GemmArgs &a,
-                             int grid, cudaStream_t s)
+template <int CL>
+static cudaError_t set_attr()
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16<CL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e == cudaSuccess && CL > 1)
+        e = cudaFuncSetAttribute(k_gemm_bf16<CL>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
+    done = e == cudaSuccess;
+    return e;
+}
+
+template <int CL>
+static cudaLaunchConfig_t config(int grid, cudaStream_t s, cudaLaunchAttribute *attr)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+int gemm_max_ctas(int cluster, int num_sms)
+{
+    if (cluster == 1) return num_sms;
+    if (set_attr<2>() != cudaSuccess) return 0;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = config<2>(2 * (num_sms / 2), nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_gemm_bf16<2>, &cfg) != cudaSuccess) return 0;
+    return 2 * n;
+}
+
+cudaError_t launch_gemm_bf16(const void *map_a, const void *map_b, const GemmArgs &a,
+                             int cluster, int grid, cudaStream_t s)
+{
     CUtensorMap ma, mb;
     memcpy(&ma, map_a, sizeof ma);
     memcpy(&mb, map_b, sizeof mb);
-    k_gemm_bf16<<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, a);
-    return cudaGetLastError();
+    cudaError_t e;
+    cudaLaunchAttribute attr[1];
+    if (cluster == 2) {
+        e = set_attr<2>();
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = config<2>(grid, s, attr);
+        e = cudaLaunchKernelEx(&cfg, k_gemm_bf16<2>, ma, mb, a);
+    } else {
+        e = set_attr<1>();
+        if (e != cudaSuccess) return e;
+        k_gemm_bf16<1><<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, a);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 }  // namespace gw

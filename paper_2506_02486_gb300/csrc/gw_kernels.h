@@ -126,8 +126,12 @@ struct GemmArgs {
 int gemm_smem_bytes();
 int gemm_tile_m();
 int gemm_tile_n();
-// map_a / map_b: host copies of the encoded tensor maps (CUtensorMap).
+// Most CTAs that can be resident at once for a cluster size (1 or 2; with 2
+// a multiple of 2); 0 on error.
+int gemm_max_ctas(int cluster, int num_sms);
+// map_a / map_b: host copies of the encoded tensor maps (CUtensorMap); the
+// B map's box is 256 / cluster rows.  grid: CTAs, a multiple of cluster.
 cudaError_t launch_gemm_bf16(const void *map_a, const void *map_b, const GemmArgs &a,
-                             int grid, cudaStream_t s);
+                             int cluster, int grid, cudaStream_t s);
 
 }  // namespace gw

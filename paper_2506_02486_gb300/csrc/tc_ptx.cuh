@@ -85,6 +85,59 @@ __device__ __forceinline__ void commit(uint64_t *bar)
         :: "r"(smem_addr(bar)) : "memory");
 }
 
+// The same arrival on the barrier at this offset in every CTA of the
+// cluster named in `mask`.
+__device__ __forceinline__ void commit_mc(uint64_t *bar, uint16_t mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster"
+        ".multicast::cluster.b64 [%0], %1;"
+        :: "r"(smem_addr(bar)), "h"(mask) : "memory");
+}
+
+// ---- clusters --------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t ncluster_x()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// All threads of all CTAs of the cluster.
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// 3-D tiled TMA load of one box written to the same shared-memory offset in
+// every CTA of the cluster named in `mask`, each completing on its own
+// barrier at the offset of `bar`.
+__device__ __forceinline__ void tma_load_3d_mc(void *dst, const void *map, uint64_t *bar,
+                                               int c0, int c1, int c2, uint16_t mask,
+                                               uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile"
+        ".mbarrier::complete_tx::bytes.multicast::cluster.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6, %7;"
+        :: "r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)),
+           "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar)), "h"(mask), "l"(policy)
+        : "memory");
+}
+
 // 32 consecutive FP32 columns of this thread's TMEM lane (32x32b shape: the
 // warp reads lanes 32 * (warp % 4) .. + 31, one lane per thread).  The load
 // and its wait are one asm statement, so no use of the outputs can be

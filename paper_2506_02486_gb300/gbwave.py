@@ -149,6 +149,7 @@ _SIGS = {
     "gw_cannon_set": [_P, _P, _P, _I],
     "gw_cannon_run": [_P, _P],
     "gw_cannon_sync": [_P],
+    "gw_cannon_set_cluster": [_P, _I],
     "gw_cannon_read_c": [_P, _P, _I],
     "gw_cannon_timing": [_P, _I],
     "gw_cannon_stats": [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
@@ -424,6 +425,10 @@ def gw_cannon_set(cn: int, a, bt, on_device: bool = False):
 
 def gw_cannon_run(cn: int, stream=None):
     _check(lib().gw_cannon_run(cn, _stream(stream)), "gw_cannon_run")
+
+
+def gw_cannon_set_cluster(cn: int, cluster: int):
+    _check(lib().gw_cannon_set_cluster(cn, int(cluster)), "gw_cannon_set_cluster")
 
 
 def gw_cannon_sync(cn: int):

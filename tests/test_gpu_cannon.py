@@ -16,12 +16,13 @@ from workloads import matmul as mm
 pytestmark = pytest.mark.gpu
 
 
-def cannon_gpu(a_bits, bt_bits, n, p, runs=1, stats=False):
+def cannon_gpu(a_bits, bt_bits, n, p, runs=1, stats=False, cluster=2):
     ensure_built()
     per = gw.gw_cannon_bytes(n, p)
     with Segment(p * (per + (1 << 20)), nranks=p) as seg:
         cn = gw.gw_cannon_create(seg.ctx, n, p)
         try:
+            gw.gw_cannon_set_cluster(cn, cluster)
             gw.gw_cannon_set(cn, a_bits, bt_bits)
             out = []
             for _ in range(runs):
@@ -35,11 +36,16 @@ def cannon_gpu(a_bits, bt_bits, n, p, runs=1, stats=False):
     return (out, pool) if stats else out
 
 
-@pytest.mark.parametrize("n,p", [(256, 2), (328, 4), (384, 3), (512, 1)])
-def test_dyadic_inputs_bit_exact(n, p):
+@pytest.mark.parametrize("cluster", [1, 2])
+@pytest.mark.parametrize("n,p", [(256, 2), (328, 4), (384, 3), (512, 1),
+                                 (1152, 3)])
+def test_dyadic_inputs_bit_exact(n, p, cluster):
+    """Ragged cases: 328 / 4 = 82 rows per stripe (one partial tile) and a
+    K tail of 8; 1152 / 3 = 384 = 3 tile rows (an odd count: the second CTA
+    of a cluster gets an empty tile)."""
     a_bits, bt_bits, a, b = mm.pair(n, 100 + n + p, "dyadic")
     ref, _ = oc.cannon(a, b, p)
-    (c,) = cannon_gpu(a_bits, bt_bits, n, p)
+    (c,) = cannon_gpu(a_bits, bt_bits, n, p, cluster=cluster)
     assert np.array_equal(c.astype(np.float64), ref)
 
 
@@ -56,10 +62,12 @@ def test_uniform_inputs_within_fp32_bound():
 
 
 def test_ring_gives_the_bits_of_the_single_product():
+    """Each element's sum runs over the same K blocks in the same order
+    whatever the stripe, tile or cluster it falls in."""
     n = 768
     a_bits, bt_bits, _, _ = mm.pair(n, 17, "uniform")
-    (one,) = cannon_gpu(a_bits, bt_bits, n, 1)
-    for p in (2, 3, 4, 6):
+    (one,) = cannon_gpu(a_bits, bt_bits, n, 1, cluster=1)
+    for p in (1, 2, 3, 4, 6):
         (c,) = cannon_gpu(a_bits, bt_bits, n, p)
         assert np.array_equal(c, one), p
 
