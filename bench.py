@@ -71,6 +71,15 @@ def measured_peak() -> tuple[float, str]:
     return 6800.0, "fallback"
 
 
+def measured_peak_tensor() -> tuple[float, str]:
+    """Dense BF16 TFLOP/s (cuBLAS burst) measured on this machine's GPUs."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (cuBLAS bf16 burst)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
 def recorded_traffic() -> float | None:
     """Per-launch DRAM bytes of the step kernel from the committed ncu
     summary, if it was taken on the current kernel sources."""
@@ -495,6 +504,7 @@ def run_ours(args, world, rank, local, pg):
                     "roofline_frac": bpp * npts / (kavg * 1e-3) / 1e9 / measured_peak()[0],
                     "steps": vs,
                 }
+            variants[f"cannon_{CANNON_N}_p{CANNON_P}"] = run_cannon(device=local)
             for dt in ("f32", "bf16"):
                 for suffix, kw in (("", {}), ("_persistent", dict(persistent=True))):
                     r = run_batch(dt, **kw)
@@ -644,6 +654,64 @@ def run_serve(n=2000, *, seed=SERVE_SEED, load=SERVE_LOAD, slots=64,
     }
 
 
+CANNON_N, CANNON_P = 30240, 4     # the paper's matrix size; 4 ring ranks
+
+
+def run_cannon(n=CANNON_N, p=CANNON_P, runs=3, cluster=2, group=16, seed=2506,
+               device=0):
+    """Cannon's ring exchange (section 5) on dyadic BF16 inputs: TFLOP/s of
+    whole runs (P ring steps each, puts overlapped) and of the block-product
+    kernel alone (per-launch CUDA events in a separate run)."""
+    import torch
+    from paper_2506_02486_gb300 import gbwave as gw
+    from paper_2506_02486_gb300.runtime import Segment
+    from workloads import matmul as mm
+    a_bits = mm.dyadic_bits(mm.dyadic_codes(n, n, seed))
+    bt_bits = mm.dyadic_bits(mm.dyadic_codes(n, n, seed + 1))
+    per = gw.gw_cannon_bytes(n, p)
+    flops = 2.0 * n ** 3
+    with Segment(p * (per + (1 << 20)), nranks=p, device=device) as seg:
+        cn = gw.gw_cannon_create(seg.ctx, n, p)
+        try:
+            gw.gw_cannon_schedule(cn, cluster, group)
+            gw.gw_cannon_set(cn, a_bits, bt_bits)
+            del a_bits, bt_bits
+            st = torch.cuda.current_stream()
+            gw.gw_cannon_run(cn, st)                  # warm-up
+            gw.gw_cannon_sync(cn)
+            gw.gw_cannon_timing(cn, True)
+            gw.gw_cannon_run(cn, st)
+            gw.gw_cannon_sync(cn)
+            k = gw.gw_cannon_stats(cn)
+            gw.gw_cannon_timing(cn, False)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(runs):
+                gw.gw_cannon_run(cn, st)
+            e1.record(st)
+            gw.gw_cannon_sync(cn)
+            ms = e0.elapsed_time(e1) / runs
+            pool = gw.gw_pool_stats_get(seg.ctx)
+        finally:
+            gw.gw_cannon_destroy(cn)
+    peak = measured_peak_tensor()
+    kms = k["gemm_ms"] / max(1, k["launches"])
+    kflops = flops / p                            # one ring step
+    return {
+        "n": n, "p": p, "cluster": cluster, "group": group, "runs": runs,
+        "inputs": "dyadic bf16",
+        "ms_per_run": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+        "kernel_ms": kms, "kernel_launches_per_run": p, "grid": k["grid"],
+        "roofline": {"bound": "tensor", "achieved": kflops / (kms * 1e-3) / 1e12,
+                     "peak": peak[0], "peak_kind": peak[1], "unit": "TFLOP/s",
+                     "frac": kflops / (kms * 1e-3) / 1e12 / peak[0]},
+        "puts_per_run": p * (p - 1),
+        "pool_peak_active": pool["peak_active"],
+    }
+
+
 def run_batch_modes(args):
     """The 64-shot workload under each schedule, one JSON line each."""
     import torch
@@ -766,7 +834,22 @@ def main():
                     help="replay N Poisson shot requests through the server")
     ap.add_argument("--batch", action="store_true",
                     help="64-shot batched workload: schedules compared")
+    ap.add_argument("--cannon", type=int, default=0, metavar="N",
+                    help="Cannon ring-exchange product of two N x N matrices")
+    ap.add_argument("--cannon-p", type=int, default=CANNON_P, help="ring ranks")
+    ap.add_argument("--cannon-cluster", type=int, default=2,
+                    help="CTAs sharing a B tile (1 or 2)")
+    ap.add_argument("--cannon-group", type=int, default=16,
+                    help="tile rows per raster group")
     args = ap.parse_args()
+    if args.cannon:
+        from paper_2506_02486_gb300 import buildlib
+        buildlib.build()
+        print(json.dumps({"cannon": run_cannon(args.cannon, args.cannon_p,
+                                               runs=max(1, args.steps if args.steps != 1000 else 3),
+                                               cluster=args.cannon_cluster,
+                                               group=args.cannon_group)}), flush=True)
+        return 0
     if args.batch:
         return run_batch_modes(args)
     if args.serve:

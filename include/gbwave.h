@@ -287,10 +287,13 @@ gw_status gw_cannon_set(gw_cannon *cn, const void *a, const void *bt,
  * all of C).  Device waits are bounded: a kernel that gave up is reported as
  * GW_ERR_TIMEOUT by gw_cannon_sync / gw_cannon_read_c. */
 gw_status gw_cannon_run(gw_cannon *cn, gw_stream stream);
-/* CTAs per cluster of the block-product kernel: 2 (default) pairs CTAs on
- * vertically adjacent tiles that share each B tile through a TMA multicast;
- * 1 loads every tile alone.  Same results either way. */
-gw_status gw_cannon_set_cluster(gw_cannon *cn, int cluster);
+/* Schedule of the block-product kernel (results are the same bits for
+ * every choice).  cluster: CTAs per cluster; 2 (default) pairs CTAs on
+ * vertically adjacent 128 x 256 tiles that share each B tile through a TMA
+ * multicast, 1 loads every tile alone.  group: tile rows per raster group
+ * (default 16), a multiple of cluster in 1 .. 1024; the CTAs running at the
+ * same time sweep a group's rows column by column. */
+gw_status gw_cannon_schedule(gw_cannon *cn, int cluster, int group);
 /* Device synchronisation and the kernel error word. */
 gw_status gw_cannon_sync(gw_cannon *cn);
 /* C (N x N, row-major FP32) to the host (on_device = 0) or the device,

@@ -28,6 +28,7 @@ struct gw_cannon {
     int off = 0;              // rank r holds B column stripe (r + off) mod p
     CUtensorMap map_a, map_b[2][2];   // [buffer][cluster size - 1]
     int cluster = 2;          // CTAs sharing one B tile (TMA multicast)
+    int group = 16;           // tile rows per raster group
     unsigned *err = nullptr;  // device error word
     gw_gptr gerr = 0;
     bool timing = false;
@@ -114,6 +115,7 @@ gw_status launch_step(gw_cannon *cn, cudaStream_t s)
     }
     a.c = reinterpret_cast<float *>(c0);
     a.ldc = cn->n;
+    a.group = cn->group;
     a.err = cn->err;
     if (cn->timing) GW_TRY_CUDA(cudaEventRecord(cn->ev0, s));
     GW_TRY_CUDA(launch_gemm_bf16(&cn->map_a, &cn->map_b[cn->cur][cn->cluster - 1], a,
@@ -210,13 +212,17 @@ gw_status gw_cannon_create(gw_ctx *c, int n, int p, gw_cannon **out)
     return GW_OK;
 }
 
-gw_status gw_cannon_set_cluster(gw_cannon *cn, int cluster)
+gw_status gw_cannon_schedule(gw_cannon *cn, int cluster, int group)
 {
     if (!cn) return fail(GW_ERR_ARG, "NULL argument");
     if (cluster != 1 && cluster != 2) return fail(GW_ERR_ARG, "cluster size must be 1 or 2");
+    if (group < cluster || group > 1024 || group % cluster)
+        return fail(GW_ERR_ARG, "group must be a multiple of the cluster size in 1 .. 1024");
     std::lock_guard<std::recursive_mutex> lk(cn->ctx->mu);
     GW_TRY_CUDA(cudaSetDevice(cn->ctx->device));
-    return set_grid(cn, cluster);
+    GW_TRY(set_grid(cn, cluster));
+    cn->group = group;
+    return GW_OK;
 }
 
 gw_status gw_cannon_destroy(gw_cannon *cn)

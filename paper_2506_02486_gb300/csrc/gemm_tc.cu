@@ -22,7 +22,7 @@
 namespace gw {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4, GROUP_M = 8;
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;            // 16 KB
 constexpr int B_BYTES = BN * BK * 2;            // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -41,8 +41,9 @@ struct TileCoord {
 };
 
 // Tile t of the launch: problems one after another; inside a problem,
-// groups of GROUP_M tile rows swept column by column, so the CTAs running
-// at the same time share A rows and B columns in L2.
+// groups of `group` tile rows swept column by column, so the CTAs running
+// at the same time share A rows and B columns in L2, and the next wave
+// reuses the group's A rows.
 __device__ __forceinline__ TileCoord tile_of(int t, int tmc, int tnc, int group)
 {
     const int per = tmc * tnc;
@@ -120,6 +121,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
     const int tmu = (tmc + CL - 1) / CL;          // tile-row units
     const int nunits = A.nprob * tmu * tnc;
     const int nkb = (A.k + BK - 1) / BK;
+    const int group_u = max(1, A.group / CL);   // units per raster group
     constexpr uint16_t kPeers = (uint16_t)((1u << CL) - 1u);
 
     if (threadIdx.x == 0) {
@@ -151,7 +153,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
             const uint64_t pol = policy_evict_normal();
             uint32_t it = 0;
             for (int u = unit0; u < nunits; u += nunit_step) {
-                const TileCoord tc_ = tile_of(u, tmu, tnc, GROUP_M / CL);
+                const TileCoord tc_ = tile_of(u, tmu, tnc, group_u);
                 const int tm = tc_.tm * CL + crank;
                 const int ra = A.a_rank[tc_.q], rb = A.b_rank[tc_.q];
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
@@ -230,7 +232,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
                 break;
             }
             tc::fence_after_sync();
-            const TileCoord tc_ = tile_of(u, tmu, tnc, GROUP_M / CL);
+            const TileCoord tc_ = tile_of(u, tmu, tnc, group_u);
             const int row = (tc_.tm * CL + crank) * BM + row_in_tile;
             const int col0 = tc_.tn * BN;
             float *crow = A.c + A.c_off[tc_.q] + (long long)row * A.ldc + col0;

@@ -121,6 +121,7 @@ struct GemmArgs {
     long long c_off[kGemmMaxProb];  // element offset of its block in c
     float *c;
     long long ldc;
+    int group;                      // tile rows per raster group (multiple of the cluster size)
     unsigned *err;                  // ERRB_TIMEOUT when a wait gave up
 };
 int gemm_smem_bytes();

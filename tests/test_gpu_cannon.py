@@ -16,13 +16,13 @@ from workloads import matmul as mm
 pytestmark = pytest.mark.gpu
 
 
-def cannon_gpu(a_bits, bt_bits, n, p, runs=1, stats=False, cluster=2):
+def cannon_gpu(a_bits, bt_bits, n, p, runs=1, stats=False, cluster=2, group=16):
     ensure_built()
     per = gw.gw_cannon_bytes(n, p)
     with Segment(p * (per + (1 << 20)), nranks=p) as seg:
         cn = gw.gw_cannon_create(seg.ctx, n, p)
         try:
-            gw.gw_cannon_set_cluster(cn, cluster)
+            gw.gw_cannon_schedule(cn, cluster, group)
             gw.gw_cannon_set(cn, a_bits, bt_bits)
             out = []
             for _ in range(runs):
@@ -70,6 +70,9 @@ def test_ring_gives_the_bits_of_the_single_product():
     for p in (1, 2, 3, 4, 6):
         (c,) = cannon_gpu(a_bits, bt_bits, n, p)
         assert np.array_equal(c, one), p
+    for cluster, group in ((1, 1), (2, 2), (1, 3), (2, 64)):
+        (c,) = cannon_gpu(a_bits, bt_bits, n, 2, cluster=cluster, group=group)
+        assert np.array_equal(c, one), (cluster, group)
 
 
 def test_repeated_runs_and_pool_use():
@@ -94,3 +97,22 @@ def test_arguments_checked():
             gw.gw_cannon_create(seg.ctx, 96, 4)  # more ranks than the segment
         with pytest.raises(gw.GWError):
             gw.gw_cannon_create(seg.ctx, 100, 2)  # rows not 16-byte multiples
+
+
+def test_paper_size_sampled_entries_exact():
+    """The paper's 30240 x 30240 product on 4 ring ranks, the launch
+    configuration the benchmark times: sampled entries against the oracle's
+    one-by-one FP64 sums (exact for dyadic inputs), plus the entries of the
+    last rows and columns (ragged tiles: 7560 = 59 x 128 + 8 rows per stripe,
+    30240 = 118 x 256 + 32 columns)."""
+    n, p = 30240, 4
+    ka = mm.dyadic_codes(n, n, 2506)
+    kb = mm.dyadic_codes(n, n, 2507)
+    (c,) = cannon_gpu(mm.dyadic_bits(ka), mm.dyadic_bits(kb), n, p)
+    rng = np.random.default_rng(1)
+    idx = [tuple(rng.integers(0, n, 2)) for _ in range(200)]
+    idx += [(n - 1, n - 1), (n - 1, 0), (0, n - 1), (7559, 7560), (7560, 7559),
+            (15119, 22679), (22680, 30239)]
+    for i, j in idx:
+        ref = oc.entry(mm.dyadic_values(ka[i:i + 1]), mm.dyadic_values(kb[j:j + 1]).T, 0, 0)
+        assert c[i, j] == ref, (i, j, c[i, j], ref)
