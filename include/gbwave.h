@@ -288,11 +288,13 @@ gw_status gw_cannon_set(gw_cannon *cn, const void *a, const void *bt,
  * GW_ERR_TIMEOUT by gw_cannon_sync / gw_cannon_read_c. */
 gw_status gw_cannon_run(gw_cannon *cn, gw_stream stream);
 /* Schedule of the block-product kernel (results are the same bits for
- * every choice).  cluster: CTAs per cluster; 2 (default) pairs CTAs on
- * vertically adjacent 128 x 256 tiles that share each B tile through a TMA
- * multicast, 1 loads every tile alone.  group: tile rows per raster group
- * (default 16), a multiple of cluster in 1 .. 1024; the CTAs running at the
- * same time sweep a group's rows column by column. */
+ * every choice).  cluster: CTAs per cluster over 128 x 256 tiles; 1 loads
+ * every tile alone, 2 (default) pairs vertically adjacent tiles that share
+ * each B tile through a TMA multicast, 4 takes a 2 x 2 block of tiles that
+ * share A and B tiles.  group: tile rows per raster group (default 16), in
+ * 1 .. 1024 and even for clusters 2 and 4; the CTAs running at the same
+ * time sweep a group's rows column by column.  GW_ERR_CUDA if the device
+ * cannot hold a cluster of that size. */
 gw_status gw_cannon_schedule(gw_cannon *cn, int cluster, int group);
 /* Device synchronisation and the kernel error word. */
 gw_status gw_cannon_sync(gw_cannon *cn);

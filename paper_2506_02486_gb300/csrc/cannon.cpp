@@ -26,7 +26,8 @@ struct gw_cannon {
     gw_gptr ga = 0, gb[2] = {0, 0}, gc = 0;
     int cur = 0;              // B buffer holding the current stripes
     int off = 0;              // rank r holds B column stripe (r + off) mod p
-    CUtensorMap map_a, map_b[2][2];   // [buffer][cluster size - 1]
+    CUtensorMap map_a[2];             // [A box: 128 or 64 rows]
+    CUtensorMap map_b[2][2];          // [buffer][B box: 256 or 128 rows]
     int cluster = 2;          // CTAs sharing one B tile (TMA multicast)
     int group = 16;           // tile rows per raster group
     unsigned *err = nullptr;  // device error word
@@ -118,8 +119,10 @@ gw_status launch_step(gw_cannon *cn, cudaStream_t s)
     a.group = cn->group;
     a.err = cn->err;
     if (cn->timing) GW_TRY_CUDA(cudaEventRecord(cn->ev0, s));
-    GW_TRY_CUDA(launch_gemm_bf16(&cn->map_a, &cn->map_b[cn->cur][cn->cluster - 1], a,
-                                 cn->cluster, cn->grid, s));
+    // cluster 1: 1 x 1; 2: 2 x 1 (B tiles shared); 4: 2 x 2 (A and B shared)
+    const int ia = cn->cluster == 4 ? 1 : 0, ib = cn->cluster >= 2 ? 1 : 0;
+    GW_TRY_CUDA(launch_gemm_bf16(&cn->map_a[ia], &cn->map_b[cn->cur][ib], a, cn->cluster,
+                                 cn->grid, s));
     if (cn->timing) {
         GW_TRY_CUDA(cudaEventRecord(cn->ev1, s));
         GW_TRY_CUDA(cudaEventSynchronize(cn->ev1));
@@ -135,9 +138,10 @@ gw_status launch_step(gw_cannon *cn, cudaStream_t s)
 // than tiles.
 gw_status set_grid(gw_cannon *cn, int cluster)
 {
+    const int cm = cluster >= 2 ? 2 : 1, cnn = cluster / cm;
     const int tm = (cn->ns + gemm_tile_m() - 1) / gemm_tile_m();
     const int tn = (cn->ns + gemm_tile_n() - 1) / gemm_tile_n();
-    const int units = cn->p * ((tm + cluster - 1) / cluster) * tn;
+    const int units = cn->p * ((tm + cm - 1) / cm) * ((tn + cnn - 1) / cnn);
     const int most = gemm_max_ctas(cluster, cn->ctx->num_sms);
     if (most < cluster) return fail(GW_ERR_CUDA, "no resident cluster of %d CTAs", cluster);
     cn->cluster = cluster;
@@ -199,10 +203,11 @@ gw_status gw_cannon_create(gw_ctx *c, int n, int p, gw_cannon **out)
     cn->err = reinterpret_cast<unsigned *>(errp);
     if (cudaMemset(cn->err, 0, sizeof(unsigned)) != cudaSuccess)
         return cleanup(fail(GW_ERR_CUDA, "error word"));
-    st = encode_stripes(cn, &cn->map_a, cn->ga, gemm_tile_m());
+    for (int h = 0; h < 2 && st == GW_OK; ++h)
+        st = encode_stripes(cn, &cn->map_a[h], cn->ga, gemm_tile_m() >> h);
     for (int b = 0; b < 2 && st == GW_OK; ++b)
-        for (int cl = 1; cl <= 2 && st == GW_OK; ++cl)
-            st = encode_stripes(cn, &cn->map_b[b][cl - 1], cn->gb[b], gemm_tile_n() / cl);
+        for (int h = 0; h < 2 && st == GW_OK; ++h)
+            st = encode_stripes(cn, &cn->map_b[b][h], cn->gb[b], gemm_tile_n() >> h);
     if (st != GW_OK) return cleanup(st);
     if (cudaEventCreate(&cn->ev0) != cudaSuccess || cudaEventCreate(&cn->ev1) != cudaSuccess)
         return cleanup(fail(GW_ERR_CUDA, "events"));
@@ -215,9 +220,11 @@ gw_status gw_cannon_create(gw_ctx *c, int n, int p, gw_cannon **out)
 gw_status gw_cannon_schedule(gw_cannon *cn, int cluster, int group)
 {
     if (!cn) return fail(GW_ERR_ARG, "NULL argument");
-    if (cluster != 1 && cluster != 2) return fail(GW_ERR_ARG, "cluster size must be 1 or 2");
-    if (group < cluster || group > 1024 || group % cluster)
-        return fail(GW_ERR_ARG, "group must be a multiple of the cluster size in 1 .. 1024");
+    if (cluster != 1 && cluster != 2 && cluster != 4)
+        return fail(GW_ERR_ARG, "cluster size must be 1, 2 or 4");
+    const int cm = cluster >= 2 ? 2 : 1;
+    if (group < cm || group > 1024 || group % cm)
+        return fail(GW_ERR_ARG, "group must be a multiple of the cluster's tile rows in 1 .. 1024");
     std::lock_guard<std::recursive_mutex> lk(cn->ctx->mu);
     GW_TRY_CUDA(cudaSetDevice(cn->ctx->device));
     GW_TRY(set_grid(cn, cluster));

@@ -90,13 +90,16 @@ __device__ __forceinline__ void give_up(volatile int *abortf, unsigned *err)
     *abortf = 1;
 }
 
-// CL = 1: one CTA per tile.  CL = 2: a cluster of two CTAs on vertically
-// adjacent tiles (tile rows 2i and 2i + 1, same tile column); each loads its
-// own A tile and one half of the shared B tile, multicast into both CTAs,
-// so a CTA fetches 32 KB from L2 per K step instead of 48 KB.  A stage may
-// then only be refilled once both CTAs' MMAs are done with it: each MMA
-// warp's commit arrives on the empty barrier of both CTAs (count 2).
-template <int CL>
+// Clusters of CM x CN CTAs on a CM x CN block of tiles (CTA rank
+// ci + CM * cj takes tile row tm0 + ci, tile column tn0 + cj).  The CN CTAs
+// of a tile row share its A tile and the CM CTAs of a tile column its B
+// tile: each CTA loads 1/CN of its A tile and 1/CM of its B tile and
+// multicasts them to the CTAs sharing them, so with 2 x 1 a CTA fetches
+// 32 KB per K step from L2 and with 2 x 2 24 KB instead of 48 KB.  A stage
+// may only be refilled once every CTA that writes into it is done with it:
+// each MMA warp's commit arrives on the empty barrier of itself and of the
+// CTAs that share its tiles (count CM + CN - 1).
+template <int CM, int CN>
 __global__ void __launch_bounds__(THREADS, 1)
 k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
             const __grid_constant__ CUtensorMap map_b,
@@ -114,20 +117,29 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
     volatile int *abortf = reinterpret_cast<volatile int *>(smem + OFF_TMEM + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int CL = CM * CN;
     const int crank = CL > 1 ? (int)tc::cluster_ctarank() : 0;
+    const int ci = crank % CM, cj = crank / CM;
     const int unit0 = CL > 1 ? (int)tc::cluster_id_x() : (int)blockIdx.x;
     const int nunit_step = CL > 1 ? (int)tc::ncluster_x() : (int)gridDim.x;
     const int tmc = (A.m + BM - 1) / BM, tnc = (A.n + BN - 1) / BN;
-    const int tmu = (tmc + CL - 1) / CL;          // tile-row units
-    const int nunits = A.nprob * tmu * tnc;
+    const int tmu = (tmc + CM - 1) / CM;          // unit rows
+    const int tnu = (tnc + CN - 1) / CN;          // unit columns
+    const int nunits = A.nprob * tmu * tnu;
     const int nkb = (A.k + BK - 1) / BK;
-    const int group_u = max(1, A.group / CL);   // units per raster group
-    constexpr uint16_t kPeers = (uint16_t)((1u << CL) - 1u);
+    const int group_u = max(1, A.group / CM);     // unit rows per raster group
+    // CTAs sharing this CTA's A tile (same ci) and its B tile (same cj)
+    uint16_t row_peers = 0, col_peers = 0;
+#pragma unroll
+    for (int j = 0; j < CN; ++j) row_peers |= (uint16_t)(1u << (ci + CM * j));
+#pragma unroll
+    for (int i = 0; i < CM; ++i) col_peers |= (uint16_t)(1u << (i + CM * cj));
+    const uint16_t writers = row_peers | col_peers;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CL);        // one commit per CTA of the cluster
+            mbar_init(&empty[s], CM + CN - 1);   // one commit per writer
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
@@ -153,8 +165,8 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
             const uint64_t pol = policy_evict_normal();
             uint32_t it = 0;
             for (int u = unit0; u < nunits; u += nunit_step) {
-                const TileCoord tc_ = tile_of(u, tmu, tnc, group_u);
-                const int tm = tc_.tm * CL + crank;
+                const TileCoord tc_ = tile_of(u, tmu, tnu, group_u);
+                const int tm = tc_.tm * CM + ci, tn = tc_.tn * CN + cj;
                 const int ra = A.a_rank[tc_.q], rb = A.b_rank[tc_.q];
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const uint32_t s = it % STAGES;
@@ -165,14 +177,18 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
                     }
                     unsigned char *st = smem + s * STAGE_BYTES;
                     mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                    tma_load_3d(st, &map_a, &full[s], kb * BK, tm * BM, ra, pol);
-                    if (CL == 1)
-                        tma_load_3d(st + A_BYTES, &map_b, &full[s], kb * BK, tc_.tn * BN,
-                                    rb, pol);
+                    if (CN == 1)
+                        tma_load_3d(st, &map_a, &full[s], kb * BK, tm * BM, ra, pol);
                     else
-                        tc::tma_load_3d_mc(st + A_BYTES + crank * (B_BYTES / CL), &map_b,
-                                           &full[s], kb * BK,
-                                           tc_.tn * BN + crank * (BN / CL), rb, kPeers, pol);
+                        tc::tma_load_3d_mc(st + cj * (A_BYTES / CN), &map_a, &full[s],
+                                           kb * BK, tm * BM + cj * (BM / CN), ra,
+                                           row_peers, pol);
+                    if (CM == 1)
+                        tma_load_3d(st + A_BYTES, &map_b, &full[s], kb * BK, tn * BN, rb, pol);
+                    else
+                        tc::tma_load_3d_mc(st + A_BYTES + ci * (B_BYTES / CM), &map_b,
+                                           &full[s], kb * BK, tn * BN + ci * (BN / CM), rb,
+                                           col_peers, pol);
                 }
             }
         produced:
@@ -211,7 +227,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
                                      (kb | kk) != 0);
                     // stage free (in every CTA that wrote into it) when done
                     if (CL == 1) tc::commit(&empty[s]);
-                    else tc::commit_mc(&empty[s], kPeers);
+                    else tc::commit_mc(&empty[s], writers);
                 }
                 if (!ok) break;
                 tc::commit(&tfull[b]);                     // accumulator ready
@@ -232,9 +248,9 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
                 break;
             }
             tc::fence_after_sync();
-            const TileCoord tc_ = tile_of(u, tmu, tnc, group_u);
-            const int row = (tc_.tm * CL + crank) * BM + row_in_tile;
-            const int col0 = tc_.tn * BN;
+            const TileCoord tc_ = tile_of(u, tmu, tnu, group_u);
+            const int row = (tc_.tm * CM + ci) * BM + row_in_tile;
+            const int col0 = (tc_.tn * CN + cj) * BN;
             float *crow = A.c + A.c_off[tc_.q] + (long long)row * A.ldc + col0;
             const bool vec = ((reinterpret_cast<uintptr_t>(crow) & 15u) == 0);
 #pragma unroll 1
@@ -276,23 +292,19 @@ int gemm_smem_bytes() { return SMEM_BYTES; }
 int gemm_tile_m() { return BM; }
 int gemm_tile_n() { return BN; }
 
-template <int CL>
+template <int CM, int CN>
 static cudaError_t set_attr()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16<CL>,
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16<CM, CN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          SMEM_BYTES);
-    if (e == cudaSuccess && CL > 1)
-        e = cudaFuncSetAttribute(k_gemm_bf16<CL>,
-                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
     done = e == cudaSuccess;
     return e;
 }
 
-template <int CL>
-static cudaLaunchConfig_t config(int grid, cudaStream_t s, cudaLaunchAttribute *attr)
+static cudaLaunchConfig_t config(int cl, int grid, cudaStream_t s, cudaLaunchAttribute *attr)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -300,7 +312,7 @@ static cudaLaunchConfig_t config(int grid, cudaStream_t s, cudaLaunchAttribute *
     cfg.dynamicSmemBytes = SMEM_BYTES;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.x = cl;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
@@ -308,15 +320,38 @@ static cudaLaunchConfig_t config(int grid, cudaStream_t s, cudaLaunchAttribute *
     return cfg;
 }
 
+template <int CM, int CN>
+static int max_ctas(int num_sms)
+{
+    constexpr int CL = CM * CN;
+    if (set_attr<CM, CN>() != cudaSuccess) return 0;
+    if (CL == 1) return num_sms;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = config(CL, CL * (num_sms / CL), nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_gemm_bf16<CM, CN>, &cfg) != cudaSuccess) return 0;
+    return CL * n;
+}
+
+template <int CM, int CN>
+static cudaError_t launch(const CUtensorMap &ma, const CUtensorMap &mb, const GemmArgs &a,
+                          int grid, cudaStream_t s)
+{
+    cudaError_t e = set_attr<CM, CN>();
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = config(CM * CN, grid, s, attr);
+    return cudaLaunchKernelEx(&cfg, k_gemm_bf16<CM, CN>, ma, mb, a);
+}
+
 int gemm_max_ctas(int cluster, int num_sms)
 {
-    if (cluster == 1) return num_sms;
-    if (set_attr<2>() != cudaSuccess) return 0;
-    cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = config<2>(2 * (num_sms / 2), nullptr, attr);
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_gemm_bf16<2>, &cfg) != cudaSuccess) return 0;
-    return 2 * n;
+    switch (cluster) {
+    case 1: return max_ctas<1, 1>(num_sms);
+    case 2: return max_ctas<2, 1>(num_sms);
+    case 4: return max_ctas<2, 2>(num_sms);
+    default: return 0;
+    }
 }
 
 cudaError_t launch_gemm_bf16(const void *map_a, const void *map_b, const GemmArgs &a,
@@ -325,20 +360,12 @@ cudaError_t launch_gemm_bf16(const void *map_a, const void *map_b, const GemmArg
     CUtensorMap ma, mb;
     memcpy(&ma, map_a, sizeof ma);
     memcpy(&mb, map_b, sizeof mb);
-    cudaError_t e;
-    cudaLaunchAttribute attr[1];
-    if (cluster == 2) {
-        e = set_attr<2>();
-        if (e != cudaSuccess) return e;
-        cudaLaunchConfig_t cfg = config<2>(grid, s, attr);
-        e = cudaLaunchKernelEx(&cfg, k_gemm_bf16<2>, ma, mb, a);
-    } else {
-        e = set_attr<1>();
-        if (e != cudaSuccess) return e;
-        k_gemm_bf16<1><<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, a);
-        e = cudaGetLastError();
+    switch (cluster) {
+    case 1: return launch<1, 1>(ma, mb, a, grid, s);
+    case 2: return launch<2, 1>(ma, mb, a, grid, s);
+    case 4: return launch<2, 2>(ma, mb, a, grid, s);
+    default: return cudaErrorInvalidValue;
     }
-    return e;
 }
 
 }  // namespace gw

@@ -127,11 +127,13 @@ struct GemmArgs {
 int gemm_smem_bytes();
 int gemm_tile_m();
 int gemm_tile_n();
-// Most CTAs that can be resident at once for a cluster size (1 or 2; with 2
-// a multiple of 2); 0 on error.
+// Clusters: 1 (one CTA per tile), 2 (2 x 1 tiles sharing B tiles), 4 (2 x 2
+// tiles sharing A and B tiles).  Most CTAs resident at once for a cluster
+// size (a multiple of it); 0 on error.
 int gemm_max_ctas(int cluster, int num_sms);
 // map_a / map_b: host copies of the encoded tensor maps (CUtensorMap); the
-// B map's box is 256 / cluster rows.  grid: CTAs, a multiple of cluster.
+// A map's box is 128 rows (64 with cluster 4), the B map's 256 rows (128
+// with clusters 2 and 4).  grid: CTAs, a multiple of the cluster size.
 cudaError_t launch_gemm_bf16(const void *map_a, const void *map_b, const GemmArgs &a,
                              int cluster, int grid, cudaStream_t s);
 

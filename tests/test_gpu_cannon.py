@@ -36,13 +36,14 @@ def cannon_gpu(a_bits, bt_bits, n, p, runs=1, stats=False, cluster=2, group=16):
     return (out, pool) if stats else out
 
 
-@pytest.mark.parametrize("cluster", [1, 2])
+@pytest.mark.parametrize("cluster", [1, 2, 4])
 @pytest.mark.parametrize("n,p", [(256, 2), (328, 4), (384, 3), (512, 1),
                                  (1152, 3)])
 def test_dyadic_inputs_bit_exact(n, p, cluster):
     """Ragged cases: 328 / 4 = 82 rows per stripe (one partial tile) and a
     K tail of 8; 1152 / 3 = 384 = 3 tile rows (an odd count: the second CTA
-    of a cluster gets an empty tile)."""
+    of a cluster gets an empty tile; with 2 x 2 clusters also an odd count
+    of tile columns)."""
     a_bits, bt_bits, a, b = mm.pair(n, 100 + n + p, "dyadic")
     ref, _ = oc.cannon(a, b, p)
     (c,) = cannon_gpu(a_bits, bt_bits, n, p, cluster=cluster)
@@ -70,7 +71,7 @@ def test_ring_gives_the_bits_of_the_single_product():
     for p in (1, 2, 3, 4, 6):
         (c,) = cannon_gpu(a_bits, bt_bits, n, p)
         assert np.array_equal(c, one), p
-    for cluster, group in ((1, 1), (2, 2), (1, 3), (2, 64)):
+    for cluster, group in ((1, 1), (2, 2), (1, 3), (2, 64), (4, 2), (4, 16)):
         (c,) = cannon_gpu(a_bits, bt_bits, n, 2, cluster=cluster, group=group)
         assert np.array_equal(c, one), (cluster, group)
 
@@ -97,6 +98,13 @@ def test_arguments_checked():
             gw.gw_cannon_create(seg.ctx, 96, 4)  # more ranks than the segment
         with pytest.raises(gw.GWError):
             gw.gw_cannon_create(seg.ctx, 100, 2)  # rows not 16-byte multiples
+        cn = gw.gw_cannon_create(seg.ctx, 96, 2)
+        try:
+            for bad in ((3, 16), (2, 3), (4, 0), (1, 2000)):
+                with pytest.raises(gw.GWError):
+                    gw.gw_cannon_schedule(cn, *bad)
+        finally:
+            gw.gw_cannon_destroy(cn)
 
 
 def test_paper_size_sampled_entries_exact():
