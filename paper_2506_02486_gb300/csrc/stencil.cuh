@@ -589,10 +589,12 @@ struct Step {
 
     // ---- arithmetic of one row of 4 points ---------------------------
     // P is the plane's phase within a trip of the z loop: its z neighbours
-    // sit at queue entries R + P - m and R + P + m.  Pair sums along x stay
-    // scalar (their operands straddle the pairs); with PK everything else
+    // sit at queue entries R + P - m and R + P + m.  With PK the arithmetic
     // runs on aligned float2 pairs, each lane rounded once to nearest, which
-    // gives the same bits as the scalar order.
+    // gives the same bits as the scalar order; the x pair sums at even
+    // distances are aligned pairs too (x[2h - m], x[2h + 1 - m]) +
+    // (x[2h + m], x[2h + 1 + m]), those at odd distances straddle the pairs
+    // and stay scalar.
     template <int P>
     __device__ __forceinline__ void laplacian_row(const G (&yv)[PY + 8], const G &lf,
                                                   const G &rt, int r, G &out)
@@ -603,11 +605,17 @@ struct Step {
         for (int m = 1; m <= 4; ++m)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
+                if (PK && (m & 1) == 0) continue;    // packed below
                 M xm = (i - m >= 0) ? yv[r + R].get(i - m) : lf.get(4 + i - m);
                 M xp = (i + m <= 3) ? yv[r + R].get(i + m) : rt.get(i + m - 4);
                 sx[m][i] = add_rn(xm, xp);
             }
         if constexpr (PK) {
+            // aligned x pairs k = -4, -2, 0, 2, 4, 6 of this row
+            auto xpair = [&](int k) -> float2 {
+                return k < 0 ? lf.pair((k + 4) >> 1)
+                             : (k < 4 ? yv[r + R].pair(k >> 1) : rt.pair((k - 4) >> 1));
+            };
             const float2 c0 = make_float2(W<M>::c0x3, W<M>::c0x3);
             const float2 c1 = make_float2(W<M>::c1, W<M>::c1);
             const float2 c2 = make_float2(W<M>::c2, W<M>::c2);
@@ -620,7 +628,9 @@ struct Step {
                 for (int m = 1; m <= 4; ++m) {
                     float2 sy = __fadd2_rn(yv[r + R - m].pair(h), yv[r + R + m].pair(h));
                     float2 sz = __fadd2_rn(Q[c - m][r].pair(h), Q[c + m][r].pair(h));
-                    S[m] = __fadd2_rn(__fadd2_rn(make_float2(sx[m][2 * h], sx[m][2 * h + 1]), sy), sz);
+                    const float2 sxp = (m & 1) ? make_float2(sx[m][2 * h], sx[m][2 * h + 1])
+                                               : __fadd2_rn(xpair(2 * h - m), xpair(2 * h + m));
+                    S[m] = __fadd2_rn(__fadd2_rn(sxp, sy), sz);
                 }
                 float2 l = __ffma2_rn(c1, S[1], __fmul2_rn(c0, yv[r + R].pair(h)));
                 l = __ffma2_rn(c2, S[2], l);
@@ -746,9 +756,13 @@ struct Step {
         // full barrier was waited on then): issued before the waits below
         const T *pl = ubuf((tg - R) % SU);
         G yv[PY + 8], lf[PY], rt[PY];
+        // the thread's own rows of the compute plane are already in the
+        // queue (entry R + P, the same bits); only the y neighbours load
 #pragma unroll
-        for (int j = 0; j < PY + 8; ++j)
-            ld_grp<T, PK>(pl + (PY * ty + j) * C::RW + HL + 4 * tx, yv[j]);
+        for (int j = 0; j < PY + 8; ++j) {
+            if (j >= R && j < R + PY) yv[j] = Q[R + P][j - R];
+            else ld_grp<T, PK>(pl + (PY * ty + j) * C::RW + HL + 4 * tx, yv[j]);
+        }
 #pragma unroll
         for (int r = 0; r < PY; ++r) {
             const T *row = pl + (PY * ty + r + R) * C::RW + HL + 4 * tx;
