@@ -202,20 +202,24 @@ gw_status plan_schedule(gw_domain *d)
 // streams (which do not wait for the legacy stream) see them.
 gw_status push_shot(gw_domain *d)
 {
-    // bounding box of the sources and receivers: items outside it skip the
-    // per-item search for them
-    for (int a = 0; a < 3; ++a) {
-        d->shot.lo[a] = 1 << 30;
-        d->shot.hi[a] = -1;
-    }
-    for (const std::vector<int4> *l : {&d->srcs, &d->recs})
-        for (const int4 &q : *l) {
+    // bounding boxes of the sources and of the receivers: items outside a
+    // box skip the per-item search of that list (separate boxes, so that a
+    // receiver plane far from the source does not make every item between
+    // them search)
+    const std::vector<int4> *lists[2] = {&d->srcs, &d->recs};
+    for (int l = 0; l < 2; ++l) {
+        for (int a = 0; a < 3; ++a) {
+            d->shot.lo[l][a] = 1 << 30;
+            d->shot.hi[l][a] = -1;
+        }
+        for (const int4 &q : *lists[l]) {
             const int c[3] = {q.x, q.y, q.z};
             for (int a = 0; a < 3; ++a) {
-                d->shot.lo[a] = std::min(d->shot.lo[a], c[a]);
-                d->shot.hi[a] = std::max(d->shot.hi[a], c[a]);
+                d->shot.lo[l][a] = std::min(d->shot.lo[l][a], c[a]);
+                d->shot.hi[l][a] = std::max(d->shot.hi[l][a], c[a]);
             }
         }
+    }
     GW_TRY_CUDA(cudaMemcpy(d->d_shot, &d->shot, sizeof(ShotDev), cudaMemcpyHostToDevice));
     GW_TRY_CUDA(cudaStreamSynchronize(nullptr));
     return GW_OK;

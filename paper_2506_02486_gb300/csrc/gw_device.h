@@ -67,8 +67,8 @@ struct ShotDev {
     int first_item, nitems;   // this shot's work items (contiguous range)
     float su, sw;          // delta storage scales (powers of two)
     float isu, isw;        // their inverses
-    int lo[3], hi[3];      // bounding box of sources and receivers (global
-                           // cells; lo > hi: none)
+    int lo[2][3], hi[2][3];   // bounding boxes of the sources [0] and of the
+                              // receivers [1] (global cells; lo > hi: none)
 };
 
 // One work item: a tile column (x0, y0) of subdomain `sub`, planes [z0, z1).

@@ -506,11 +506,13 @@ struct Step {
             int cnt = 0;
             int gxa = sd->gx0 + x0, gya = sd->gy0 + y0, gza = sd->gz0;
             int xl_end = min(TX, nx - x0), yl_end = min(TY, ny - y0);
-            // only items that meet the shot's source/receiver box search it
-            const bool meets = gxa <= sh->hi[0] && gxa + xl_end - 1 >= sh->lo[0] &&
-                               gya <= sh->hi[1] && gya + yl_end - 1 >= sh->lo[1] &&
-                               gza + z0 <= sh->hi[2] && gza + z1 - 1 >= sh->lo[2];
-            for (int pass = 0; meets && pass < 2; ++pass) {
+            for (int pass = 0; pass < 2; ++pass) {
+                // only items that meet the box of the list search it
+                const int *lo = sh->lo[pass], *hi = sh->hi[pass];
+                if (!(gxa <= hi[0] && gxa + xl_end - 1 >= lo[0] &&
+                      gya <= hi[1] && gya + yl_end - 1 >= lo[1] &&
+                      gza + z0 <= hi[2] && gza + z1 - 1 >= lo[2]))
+                    continue;
                 int nlist = pass == 0 ? sh->nsrc : sh->nrec;
                 const int4 *list = pass == 0 ? sh->src : sh->rec;
                 for (int b = 0; b < nlist; b += 32) {
