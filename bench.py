@@ -657,8 +657,8 @@ def run_serve(n=2000, *, seed=SERVE_SEED, load=SERVE_LOAD, slots=64,
 CANNON_N, CANNON_P = 30240, 4     # the paper's matrix size; 4 ring ranks
 
 
-def run_cannon(n=CANNON_N, p=CANNON_P, runs=3, cluster=2, group=16, seed=2506,
-               device=0):
+def run_cannon(n=CANNON_N, p=CANNON_P, runs=3, cluster=2, group=16, bk=64,
+               seed=2506, device=0):
     """Cannon's ring exchange (section 5) on dyadic BF16 inputs: TFLOP/s of
     whole runs (P ring steps each, puts overlapped) and of the block-product
     kernel alone (per-launch CUDA events in a separate run)."""
@@ -673,7 +673,7 @@ def run_cannon(n=CANNON_N, p=CANNON_P, runs=3, cluster=2, group=16, seed=2506,
     with Segment(p * (per + (1 << 20)), nranks=p, device=device) as seg:
         cn = gw.gw_cannon_create(seg.ctx, n, p)
         try:
-            gw.gw_cannon_schedule(cn, cluster, group)
+            gw.gw_cannon_schedule(cn, cluster, group, bk)
             gw.gw_cannon_set(cn, a_bits, bt_bits)
             del a_bits, bt_bits
             st = torch.cuda.current_stream()
@@ -700,7 +700,7 @@ def run_cannon(n=CANNON_N, p=CANNON_P, runs=3, cluster=2, group=16, seed=2506,
     kms = k["gemm_ms"] / max(1, k["launches"])
     kflops = flops / p                            # one ring step
     return {
-        "n": n, "p": p, "cluster": cluster, "group": group, "runs": runs,
+        "n": n, "p": p, "cluster": cluster, "group": group, "bk": bk, "runs": runs,
         "inputs": "dyadic bf16",
         "ms_per_run": ms, "tflops": flops / (ms * 1e-3) / 1e12,
         "kernel_ms": kms, "kernel_launches_per_run": p, "grid": k["grid"],
@@ -841,6 +841,8 @@ def main():
                     help="CTAs sharing a B tile (1 or 2)")
     ap.add_argument("--cannon-group", type=int, default=16,
                     help="tile rows per raster group")
+    ap.add_argument("--cannon-bk", type=int, default=64,
+                    help="K depth of a pipeline stage (64 or 32)")
     args = ap.parse_args()
     if args.cannon:
         from paper_2506_02486_gb300 import buildlib
@@ -848,7 +850,8 @@ def main():
         print(json.dumps({"cannon": run_cannon(args.cannon, args.cannon_p,
                                                runs=max(1, args.steps if args.steps != 1000 else 3),
                                                cluster=args.cannon_cluster,
-                                               group=args.cannon_group)}), flush=True)
+                                               group=args.cannon_group,
+                                               bk=args.cannon_bk)}), flush=True)
         return 0
     if args.batch:
         return run_batch_modes(args)

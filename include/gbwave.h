@@ -293,9 +293,10 @@ gw_status gw_cannon_run(gw_cannon *cn, gw_stream stream);
  * each B tile through a TMA multicast, 4 takes a 2 x 2 block of tiles that
  * share A and B tiles.  group: tile rows per raster group (default 16), in
  * 1 .. 1024 and even for clusters 2 and 4; the CTAs running at the same
- * time sweep a group's rows column by column.  GW_ERR_CUDA if the device
- * cannot hold a cluster of that size. */
-gw_status gw_cannon_schedule(gw_cannon *cn, int cluster, int group);
+ * time sweep a group's rows column by column.  bk: K depth of one pipeline
+ * stage, 64 (default: 4 stages of 48 KB) or 32 (9 stages of 24 KB).
+ * GW_ERR_CUDA if the device cannot hold a cluster of that size. */
+gw_status gw_cannon_schedule(gw_cannon *cn, int cluster, int group, int bk);
 /* Device synchronisation and the kernel error word. */
 gw_status gw_cannon_sync(gw_cannon *cn);
 /* C (N x N, row-major FP32) to the host (on_device = 0) or the device,

@@ -22,19 +22,36 @@
 namespace gw {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2;            // 16 KB
-constexpr int B_BYTES = BN * BK * 2;            // 32 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int BM = 128, BN = 256;
 constexpr int THREADS = 192;
 constexpr uint32_t TMEM_COLS = 2 * BN;          // two accumulators
-// barriers: full[S], empty[S], tfull[2], tempty[2], drain; then the TMEM
-// base address and an abort flag
-constexpr int OFF_BAR = STAGES * STAGE_BYTES;
-constexpr int NBAR = 2 * STAGES + 5;
-constexpr int OFF_TMEM = OFF_BAR + 8 * NBAR;
-constexpr int SMEM_USED = OFF_TMEM + 16;
-constexpr int SMEM_BYTES = SMEM_USED + 1024;    // + alignment of the ring
+
+// Stage shape for a K depth of BK BF16 per stage: 64 (128-byte rows,
+// 128-byte swizzle, 4 stages of 48 KB) or 32 (64-byte rows, 64-byte
+// swizzle, 9 stages of 24 KB: the same bytes in flight, refilled in finer
+// steps, so the loads run further ahead of the MMAs).
+template <int BK_>
+struct Shape {
+    static constexpr int BK = BK_;
+    static constexpr int STAGES = BK == 64 ? 4 : 9;
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    // barriers: full[S], empty[S], tfull[2], tempty[2], drain; then the
+    // TMEM base address and an abort flag
+    static constexpr int OFF_BAR = STAGES * STAGE_BYTES;
+    static constexpr int NBAR = 2 * STAGES + 5;
+    static constexpr int OFF_TMEM = OFF_BAR + 8 * NBAR;
+    static constexpr int SMEM_BYTES = OFF_TMEM + 16 + 1024;   // + ring alignment
+    static_assert(SMEM_BYTES <= 232448, "shared memory");
+};
+
+// Operand descriptor of a K-major tile of rows of BK BF16 (see tc_ptx.cuh).
+template <int BK>
+__device__ __forceinline__ uint64_t sdesc(const void *tile)
+{
+    return BK == 64 ? tc::sdesc_k128(tile) : tc::sdesc_k64(tile);
+}
 
 struct TileCoord {
     int q, tm, tn;
@@ -99,22 +116,25 @@ __device__ __forceinline__ void give_up(volatile int *abortf, unsigned *err)
 // may only be refilled once every CTA that writes into it is done with it:
 // each MMA warp's commit arrives on the empty barrier of itself and of the
 // CTAs that share its tiles (count CM + CN - 1).
-template <int CM, int CN>
+template <int CM, int CN, int BK_>
 __global__ void __launch_bounds__(THREADS, 1)
 k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
             const __grid_constant__ CUtensorMap map_b,
             const __grid_constant__ GemmArgs A)
 {
+    using SH = Shape<BK_>;
+    constexpr int BK = SH::BK, STAGES = SH::STAGES, A_BYTES = SH::A_BYTES,
+                  B_BYTES = SH::B_BYTES, STAGE_BYTES = SH::STAGE_BYTES;
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte alignment: the swizzle pattern repeats every 8 rows of 128 B
     // (the same offset in every CTA, as multicast requires)
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SH::OFF_BAR);
     uint64_t *full = bars, *empty = bars + STAGES;
     uint64_t *tfull = bars + 2 * STAGES, *tempty = tfull + 2, *drain = tempty + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + OFF_TMEM);
-    volatile int *abortf = reinterpret_cast<volatile int *>(smem + OFF_TMEM + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SH::OFF_TMEM);
+    volatile int *abortf = reinterpret_cast<volatile int *>(smem + SH::OFF_TMEM + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int CL = CM * CN;
@@ -219,8 +239,8 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
                     }
                     tc::fence_after_sync();
                     const unsigned char *st = smem + s * STAGE_BYTES;
-                    const uint64_t ad = tc::sdesc_k128(st);
-                    const uint64_t bd = tc::sdesc_k128(st + A_BYTES);
+                    const uint64_t ad = sdesc<BK>(st);
+                    const uint64_t bd = sdesc<BK>(st + A_BYTES);
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk)   // 32 bytes along K each
                         tc::mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc,
@@ -288,28 +308,28 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
 
 }  // namespace
 
-int gemm_smem_bytes() { return SMEM_BYTES; }
 int gemm_tile_m() { return BM; }
 int gemm_tile_n() { return BN; }
 
-template <int CM, int CN>
+template <int CM, int CN, int BK>
 static cudaError_t set_attr()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16<CM, CN>,
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16<CM, CN, BK>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
+                                         Shape<BK>::SMEM_BYTES);
     done = e == cudaSuccess;
     return e;
 }
 
-static cudaLaunchConfig_t config(int cl, int grid, cudaStream_t s, cudaLaunchAttribute *attr)
+static cudaLaunchConfig_t config(int cl, int grid, int smem, cudaStream_t s,
+                                 cudaLaunchAttribute *attr)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = cl;
@@ -320,50 +340,58 @@ static cudaLaunchConfig_t config(int cl, int grid, cudaStream_t s, cudaLaunchAtt
     return cfg;
 }
 
-template <int CM, int CN>
+template <int CM, int CN, int BK>
 static int max_ctas(int num_sms)
 {
     constexpr int CL = CM * CN;
-    if (set_attr<CM, CN>() != cudaSuccess) return 0;
+    if (set_attr<CM, CN, BK>() != cudaSuccess) return 0;
     if (CL == 1) return num_sms;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = config(CL, CL * (num_sms / CL), nullptr, attr);
+    cudaLaunchConfig_t cfg = config(CL, CL * (num_sms / CL), Shape<BK>::SMEM_BYTES, nullptr, attr);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_gemm_bf16<CM, CN>, &cfg) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_gemm_bf16<CM, CN, BK>, &cfg) != cudaSuccess)
+        return 0;
     return CL * n;
 }
 
-template <int CM, int CN>
+template <int CM, int CN, int BK>
 static cudaError_t launch(const CUtensorMap &ma, const CUtensorMap &mb, const GemmArgs &a,
                           int grid, cudaStream_t s)
 {
-    cudaError_t e = set_attr<CM, CN>();
+    cudaError_t e = set_attr<CM, CN, BK>();
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = config(CM * CN, grid, s, attr);
-    return cudaLaunchKernelEx(&cfg, k_gemm_bf16<CM, CN>, ma, mb, a);
+    cudaLaunchConfig_t cfg = config(CM * CN, grid, Shape<BK>::SMEM_BYTES, s, attr);
+    return cudaLaunchKernelEx(&cfg, k_gemm_bf16<CM, CN, BK>, ma, mb, a);
 }
 
-int gemm_max_ctas(int cluster, int num_sms)
+int gemm_max_ctas(int cluster, int bk, int num_sms)
 {
-    switch (cluster) {
-    case 1: return max_ctas<1, 1>(num_sms);
-    case 2: return max_ctas<2, 1>(num_sms);
-    case 4: return max_ctas<2, 2>(num_sms);
+    const int key = cluster * 100 + bk;
+    switch (key) {
+    case 164: return max_ctas<1, 1, 64>(num_sms);
+    case 264: return max_ctas<2, 1, 64>(num_sms);
+    case 464: return max_ctas<2, 2, 64>(num_sms);
+    case 132: return max_ctas<1, 1, 32>(num_sms);
+    case 232: return max_ctas<2, 1, 32>(num_sms);
+    case 432: return max_ctas<2, 2, 32>(num_sms);
     default: return 0;
     }
 }
 
 cudaError_t launch_gemm_bf16(const void *map_a, const void *map_b, const GemmArgs &a,
-                             int cluster, int grid, cudaStream_t s)
+                             int cluster, int bk, int grid, cudaStream_t s)
 {
     CUtensorMap ma, mb;
     memcpy(&ma, map_a, sizeof ma);
     memcpy(&mb, map_b, sizeof mb);
-    switch (cluster) {
-    case 1: return launch<1, 1>(ma, mb, a, grid, s);
-    case 2: return launch<2, 1>(ma, mb, a, grid, s);
-    case 4: return launch<2, 2>(ma, mb, a, grid, s);
+    switch (cluster * 100 + bk) {
+    case 164: return launch<1, 1, 64>(ma, mb, a, grid, s);
+    case 264: return launch<2, 1, 64>(ma, mb, a, grid, s);
+    case 464: return launch<2, 2, 64>(ma, mb, a, grid, s);
+    case 132: return launch<1, 1, 32>(ma, mb, a, grid, s);
+    case 232: return launch<2, 1, 32>(ma, mb, a, grid, s);
+    case 432: return launch<2, 2, 32>(ma, mb, a, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -124,17 +124,18 @@ struct GemmArgs {
     int group;                      // tile rows per raster group (multiple of the cluster size)
     unsigned *err;                  // ERRB_TIMEOUT when a wait gave up
 };
-int gemm_smem_bytes();
 int gemm_tile_m();
 int gemm_tile_n();
 // Clusters: 1 (one CTA per tile), 2 (2 x 1 tiles sharing B tiles), 4 (2 x 2
-// tiles sharing A and B tiles).  Most CTAs resident at once for a cluster
-// size (a multiple of it); 0 on error.
-int gemm_max_ctas(int cluster, int num_sms);
-// map_a / map_b: host copies of the encoded tensor maps (CUtensorMap); the
-// A map's box is 128 rows (64 with cluster 4), the B map's 256 rows (128
-// with clusters 2 and 4).  grid: CTAs, a multiple of the cluster size.
+// tiles sharing A and B tiles).  bk: K depth of a pipeline stage, 64 (4
+// stages, 128-byte swizzle) or 32 (9 stages, 64-byte swizzle).  Most CTAs
+// resident at once (a multiple of the cluster size); 0 on error.
+int gemm_max_ctas(int cluster, int bk, int num_sms);
+// map_a / map_b: host copies of the encoded tensor maps (CUtensorMap) with
+// a box of bk elements along K (swizzle 2 bk bytes) and 128 A rows (64 with
+// cluster 4) or 256 B rows (128 with clusters 2 and 4).  grid: CTAs, a
+// multiple of the cluster size.
 cudaError_t launch_gemm_bf16(const void *map_a, const void *map_b, const GemmArgs &a,
-                             int cluster, int grid, cudaStream_t s);
+                             int cluster, int bk, int grid, cudaStream_t s);
 
 }  // namespace gw

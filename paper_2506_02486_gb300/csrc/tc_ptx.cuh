@@ -52,6 +52,16 @@ __device__ __forceinline__ uint64_t sdesc_k128(const void *tile)
            (1ull << 46) | (2ull << 61);
 }
 
+// The same for rows of 64 bytes (32 BF16 along K) written with 64-byte
+// swizzling: 8-row atoms of 512 bytes (stride byte offset 512), swizzle
+// mode 4 (64 B).
+__device__ __forceinline__ uint64_t sdesc_k64(const void *tile)
+{
+    const uint64_t a = smem_addr(tile);
+    return ((a >> 4) & 0x3FFFull) | (1ull << 16) | ((512ull >> 4) << 32) |
+           (1ull << 46) | (4ull << 61);
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
 // both operands K-major: D format bits 4-5 = 1 (F32), A format bits 7-9 =
 // 1 (BF16), B format bits 10-12 = 1 (BF16), N / 8 in bits 17-22, M / 16 in

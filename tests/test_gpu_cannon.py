@@ -16,13 +16,14 @@ from workloads import matmul as mm
 pytestmark = pytest.mark.gpu
 
 
-def cannon_gpu(a_bits, bt_bits, n, p, runs=1, stats=False, cluster=2, group=16):
+def cannon_gpu(a_bits, bt_bits, n, p, runs=1, stats=False, cluster=2, group=16,
+               bk=64):
     ensure_built()
     per = gw.gw_cannon_bytes(n, p)
     with Segment(p * (per + (1 << 20)), nranks=p) as seg:
         cn = gw.gw_cannon_create(seg.ctx, n, p)
         try:
-            gw.gw_cannon_schedule(cn, cluster, group)
+            gw.gw_cannon_schedule(cn, cluster, group, bk)
             gw.gw_cannon_set(cn, a_bits, bt_bits)
             out = []
             for _ in range(runs):
@@ -36,17 +37,18 @@ def cannon_gpu(a_bits, bt_bits, n, p, runs=1, stats=False, cluster=2, group=16):
     return (out, pool) if stats else out
 
 
-@pytest.mark.parametrize("cluster", [1, 2, 4])
+@pytest.mark.parametrize("cluster,bk", [(1, 64), (2, 64), (4, 64), (1, 32),
+                                        (2, 32)])
 @pytest.mark.parametrize("n,p", [(256, 2), (328, 4), (384, 3), (512, 1),
                                  (1152, 3)])
-def test_dyadic_inputs_bit_exact(n, p, cluster):
+def test_dyadic_inputs_bit_exact(n, p, cluster, bk):
     """Ragged cases: 328 / 4 = 82 rows per stripe (one partial tile) and a
     K tail of 8; 1152 / 3 = 384 = 3 tile rows (an odd count: the second CTA
     of a cluster gets an empty tile; with 2 x 2 clusters also an odd count
     of tile columns)."""
     a_bits, bt_bits, a, b = mm.pair(n, 100 + n + p, "dyadic")
     ref, _ = oc.cannon(a, b, p)
-    (c,) = cannon_gpu(a_bits, bt_bits, n, p, cluster=cluster)
+    (c,) = cannon_gpu(a_bits, bt_bits, n, p, cluster=cluster, bk=bk)
     assert np.array_equal(c.astype(np.float64), ref)
 
 
@@ -71,9 +73,12 @@ def test_ring_gives_the_bits_of_the_single_product():
     for p in (1, 2, 3, 4, 6):
         (c,) = cannon_gpu(a_bits, bt_bits, n, p)
         assert np.array_equal(c, one), p
-    for cluster, group in ((1, 1), (2, 2), (1, 3), (2, 64), (4, 2), (4, 16)):
-        (c,) = cannon_gpu(a_bits, bt_bits, n, 2, cluster=cluster, group=group)
-        assert np.array_equal(c, one), (cluster, group)
+    for cluster, group, bk in ((1, 1, 64), (2, 2, 64), (1, 3, 64), (2, 64, 64),
+                               (4, 2, 64), (4, 16, 64), (2, 16, 32), (1, 8, 32),
+                               (4, 16, 32)):
+        (c,) = cannon_gpu(a_bits, bt_bits, n, 2, cluster=cluster, group=group,
+                          bk=bk)
+        assert np.array_equal(c, one), (cluster, group, bk)
 
 
 def test_repeated_runs_and_pool_use():
@@ -100,7 +105,8 @@ def test_arguments_checked():
             gw.gw_cannon_create(seg.ctx, 100, 2)  # rows not 16-byte multiples
         cn = gw.gw_cannon_create(seg.ctx, 96, 2)
         try:
-            for bad in ((3, 16), (2, 3), (4, 0), (1, 2000)):
+            for bad in ((3, 16, 64), (2, 3, 64), (4, 0, 64), (1, 2000, 64),
+                        (2, 16, 48)):
                 with pytest.raises(gw.GWError):
                     gw.gw_cannon_schedule(cn, *bad)
         finally:
