@@ -302,6 +302,13 @@ gw_status gw_cannon_sync(gw_cannon *cn);
 /* C (N x N, row-major FP32) to the host (on_device = 0) or the device,
  * after a device synchronisation. */
 gw_status gw_cannon_read_c(gw_cannon *cn, void *out, int on_device);
+/* Failure-detection self-test of the block-product kernel: one launch whose
+ * producer issues no loads, so every wait of the MMA and epilogue warps
+ * runs out after limit_us (1 us .. 2 s) and the kernel latches a timeout,
+ * drains, frees its tensor memory and returns.  *expired = 1 when it did;
+ * then returns GW_ERR_TIMEOUT and the context stays usable (the error word
+ * is cleared). */
+gw_status gw_cannon_selftest_timeout(gw_cannon *cn, unsigned limit_us, int *expired);
 /* Per-launch CUDA-event timing of the block-product kernel (synchronises
  * after each launch while enabled; resets the counters). */
 gw_status gw_cannon_timing(gw_cannon *cn, int enable);

@@ -99,7 +99,9 @@ gw_status check_err(gw_cannon *cn)
 }
 
 // One step: the block products of every rank with the stripes it holds.
-gw_status launch_step(gw_cannon *cn, cudaStream_t s)
+// skip_loads / wait_ns: the bounded-wait self-test.
+gw_status launch_step(gw_cannon *cn, cudaStream_t s, int skip_loads = 0,
+                      unsigned long long wait_ns = kWaitLimitNsHost)
 {
     GemmArgs a;
     std::memset(&a, 0, sizeof a);
@@ -121,6 +123,8 @@ gw_status launch_step(gw_cannon *cn, cudaStream_t s)
     a.ldc = cn->n;
     a.group = cn->group;
     a.err = cn->err;
+    a.wait_ns = wait_ns;
+    a.skip_loads = skip_loads;
     if (cn->timing) GW_TRY_CUDA(cudaEventRecord(cn->ev0, s));
     // cluster 1: 1 x 1; 2: 2 x 1 (B tiles shared); 4: 2 x 2 (A and B shared)
     const int ia = cn->cluster == 4 ? 1 : 0, ib = cn->cluster >= 2 ? 1 : 0;
@@ -326,6 +330,28 @@ gw_status gw_cannon_sync(gw_cannon *cn)
     GW_TRY_CUDA(cudaSetDevice(cn->ctx->device));
     GW_TRY_CUDA(cudaDeviceSynchronize());
     return check_err(cn);
+}
+
+gw_status gw_cannon_selftest_timeout(gw_cannon *cn, unsigned limit_us, int *expired)
+{
+    if (!cn || !expired) return fail(GW_ERR_ARG, "NULL argument");
+    if (limit_us == 0 || limit_us > 2000000u) return fail(GW_ERR_ARG, "limit must be 1 us .. 2 s");
+    std::lock_guard<std::recursive_mutex> lk(cn->ctx->mu);
+    GW_TRY_CUDA(cudaSetDevice(cn->ctx->device));
+    GW_TRY_CUDA(cudaDeviceSynchronize());
+    GW_TRY_CUDA(cudaMemset(cn->err, 0, sizeof(unsigned)));
+    const bool timing = cn->timing;
+    cn->timing = false;
+    gw_status st = launch_step(cn, nullptr, 1, (unsigned long long)limit_us * 1000ull);
+    cn->timing = timing;
+    GW_TRY(st);
+    GW_TRY_CUDA(cudaDeviceSynchronize());
+    unsigned e = 0;
+    GW_TRY_CUDA(cudaMemcpy(&e, cn->err, sizeof e, cudaMemcpyDeviceToHost));
+    GW_TRY_CUDA(cudaMemset(cn->err, 0, sizeof(unsigned)));
+    *expired = (e & ERRB_TIMEOUT) ? 1 : 0;
+    if (*expired) return fail(GW_ERR_TIMEOUT, "block-product waits gave up as intended");
+    return GW_OK;
 }
 
 gw_status gw_cannon_timing(gw_cannon *cn, int enable)

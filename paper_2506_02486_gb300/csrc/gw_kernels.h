@@ -108,6 +108,10 @@ cudaError_t launch_check_sum(const double *part, int nplanes, double *out,
 
 // ---- tensor-core block products (gemm_tc.cu) ----
 
+// Bound of the block-product kernel's waits in normal launches (the same
+// 4 s as the step kernel's device-side limit).
+constexpr unsigned long long kWaitLimitNsHost = 4000000000ull;
+
 // C_q = A_q B_q^T for up to kGemmMaxProb problems of one shape: A_q is an
 // m x k BF16 stripe and B_q an n x k BF16 stripe (both K contiguous), read
 // through 3-D tensor maps {k, rows, rank} (128-byte swizzle; boxes 64 x 128
@@ -123,6 +127,8 @@ struct GemmArgs {
     long long ldc;
     int group;                      // tile rows per raster group (multiple of the cluster size)
     unsigned *err;                  // ERRB_TIMEOUT when a wait gave up
+    unsigned long long wait_ns;     // bound of every wait (kWaitLimitNs normally)
+    int skip_loads;                 // self-test: issue no loads, so the waits run out
 };
 int gemm_tile_m();
 int gemm_tile_n();

@@ -152,6 +152,7 @@ _SIGS = {
     "gw_cannon_schedule": [_P, _I, _I, _I],
     "gw_cannon_read_c": [_P, _P, _I],
     "gw_cannon_timing": [_P, _I],
+    "gw_cannon_selftest_timeout": [_P, ctypes.c_uint, ctypes.POINTER(_I)],
     "gw_cannon_stats": [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
                         ctypes.POINTER(_I)],
     "gw_domain_create": [_P, ctypes.POINTER(gw_shot_desc), _I, _I, _I, _P,
@@ -440,6 +441,16 @@ def gw_cannon_read_c(cn: int, out, on_device: bool = False):
     _check(lib().gw_cannon_read_c(cn, _ptr(out), int(bool(on_device))),
            "gw_cannon_read_c")
     return out
+
+
+def gw_cannon_selftest_timeout(cn: int, limit_us: int):
+    """(status, expired) of the block-product kernel's timeout self-test;
+    a status of GW_ERR_TIMEOUT is the expected outcome, not raised."""
+    e = _I()
+    st = lib().gw_cannon_selftest_timeout(cn, int(limit_us), ctypes.byref(e))
+    if st not in (GW_OK, GW_ERR_TIMEOUT):
+        _check(st, "gw_cannon_selftest_timeout")
+    return st, e.value
 
 
 def gw_cannon_timing(cn: int, enable: bool):

@@ -32,3 +32,34 @@ def test_device_waits_give_up_and_the_context_survives():
         b = gpu_run(vel, 12, src=(12, 12, 12), f_peak=40.0)
         assert np.abs(a["u"]).max() > 0
         assert np.array_equal(a["u32"], b["u32"])
+
+
+def test_block_product_waits_give_up_and_the_context_survives():
+    """The tensor-core kernel of the Cannon ring: a launch whose producer
+    issues no loads runs its MMA and epilogue waits out (50 ms), latches
+    the timeout, frees its tensor memory and returns; in both cluster modes
+    the next run is exact."""
+    ensure_built()
+    from oracle import cannon as oc
+    from paper_2506_02486_gb300.runtime import Segment
+    from workloads import matmul as mm
+    n, p = 256, 2
+    a_bits, bt_bits, a, b = mm.pair(n, 31, "dyadic")
+    ref, _ = oc.cannon(a, b, p)
+    with Segment(p * (gw.gw_cannon_bytes(n, p) + (1 << 20)), nranks=p) as seg:
+        cn = gw.gw_cannon_create(seg.ctx, n, p)
+        try:
+            gw.gw_cannon_set(cn, a_bits, bt_bits)
+            for cluster in (2, 1):
+                gw.gw_cannon_schedule(cn, cluster, 16, 64)
+                t0 = time.perf_counter()
+                st, expired = gw.gw_cannon_selftest_timeout(cn, 50000)
+                el = time.perf_counter() - t0
+                assert st == gw.GW_ERR_TIMEOUT and expired == 1
+                assert 0.04 <= el < 10.0
+                gw.gw_cannon_run(cn)
+                c = np.empty((n, n), dtype=np.float32)
+                gw.gw_cannon_read_c(cn, c)
+                assert np.array_equal(c.astype(np.float64), ref)
+        finally:
+            gw.gw_cannon_destroy(cn)
