@@ -99,3 +99,24 @@ def test_host_context_nbi_copies_and_limits(lib):
             gw.gw_set_max_active_streams(s.ctx, 0)
     finally:
         s.close()
+
+
+def test_cannon_sizes_and_host_context_refusal(lib):
+    """Host-side checks of the Cannon ring's boundary (section 5): segment
+    bytes per rank (an A stripe, two B stripe buffers, a C stripe), argument
+    validation, and a host-only context refused (the ring needs a device)."""
+    n, p = 30240, 4
+    ns = n // p
+    per = gw.gw_cannon_bytes(n, p)
+    assert per >= 3 * ns * n * 2 + ns * n * 4
+    assert per <= 3 * ns * n * 2 + ns * n * 4 + 4096
+    for bad in ((100, 3), (0, 1), (64, 0), (128, 65)):
+        with pytest.raises(gw.GWError):
+            gw.gw_cannon_bytes(*bad)
+    s = HostSeg(1 << 20, 2)
+    try:
+        with pytest.raises(gw.GWError) as e:
+            gw.gw_cannon_create(s.ctx, 64, 2)
+        assert e.value.status == gw.GW_ERR_STATE
+    finally:
+        s.close()
