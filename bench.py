@@ -505,6 +505,7 @@ def run_ours(args, world, rank, local, pg):
                     "steps": vs,
                 }
             variants[f"cannon_{CANNON_N}_p{CANNON_P}"] = run_cannon(device=local)
+            variants[f"f32_{MINIMOD_N}cubed"] = run_minimod_size(device=local)
             for dt in ("f32", "bf16"):
                 for suffix, kw in (("", {}), ("_persistent", dict(persistent=True))):
                     r = run_batch(dt, **kw)
@@ -655,6 +656,43 @@ def run_serve(n=2000, *, seed=SERVE_SEED, load=SERVE_LOAD, slots=64,
 
 
 CANNON_N, CANNON_P = 30240, 4     # the paper's matrix size; 4 ring ranks
+MINIMOD_N = 1200                  # the paper's Minimod grid (section 4.5)
+
+
+def run_minimod_size(steps=100, warmup=5, seed=2506, device=0):
+    """FP32 Gpts/s on the paper's own Minimod grid, 1200^3 (8-layer model
+    set per plane, 20-cell sponge, 20 Hz source, 64 receivers): fields
+    3 x 7 GB, device-resident, per-launch CUDA events."""
+    import torch
+    import workloads
+    from paper_2506_02486_gb300 import gbwave as gw
+    from paper_2506_02486_gb300.runtime import Segment, Shot
+    n = MINIMOD_N
+    vz = workloads.layered_profile(n, seed)
+    src = workloads.source_position(seed + 1, n, n, n, margin=20)
+    rec = workloads.lattice_receivers(n, n, 20, n=8, margin=20)
+    with Segment(seg_bytes(n, n, n, "f32"), device=device) as seg:
+        with Shot(seg, n, n, n, nsteps=steps + warmup, sponge=20) as s:
+            gw.gw_set_model_layered(s.dom, vz)
+            s.add_ricker(src, 20.0)
+            s.set_receivers(rec)
+            st = torch.cuda.current_stream()
+            s.step(warmup, st)
+            gw.gw_barrier(s.dom, st, True)
+            gw.gw_kernel_timing(s.dom, True)
+            gw.gw_kernel_stats_get(s.dom)
+            s.step(steps, st)
+            gw.gw_barrier(s.dom, st, True)
+            k = gw.gw_kernel_stats_get(s.dom)
+            gw.gw_kernel_timing(s.dom, False)
+            info = s.info
+    kms = k["total_ms"] / max(1, k["launches"])
+    npts = n ** 3
+    return {"grid": [n, n, n], "steps": steps, "gpts": npts / (kms * 1e-3) / 1e9,
+            "kernel_ms": kms, "alg_bytes_per_point": ALG_BYTES_PER_POINT,
+            "roofline_frac": ALG_BYTES_PER_POINT * npts / (kms * 1e-3) / 1e9 /
+                             measured_peak()[0],
+            "tile": info["tile"], "items": info["items"]}
 
 
 def run_cannon(n=CANNON_N, p=CANNON_P, runs=3, cluster=2, group=16, bk=64,
