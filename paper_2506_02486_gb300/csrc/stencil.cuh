@@ -846,7 +846,7 @@ struct Step {
                     }
                 }
             }
-            if (item_puts) put_halo_row(x0 + 4 * tx, y0 + PY * ty + r, z, so);
+            if (PUTS && item_puts) put_halo_row(x0 + 4 * tx, y0 + PY * ty + r, z, so);
         }
         if (locz) record_receivers(z, un);
         ust += plane_;
@@ -1009,13 +1009,16 @@ struct Step {
                 begin_item(it);
                 fill_one<0>(); fill_one<1>(); fill_one<2>(); fill_one<3>();
                 fill_one<4>(); fill_one<5>(); fill_one<6>(); fill_one<7>();
-                // three loop bodies: whole tiles without puts (sources and
+                // four loop bodies: whole tiles without puts (sources and
                 // receivers handled on their planes), whole tiles with puts
-                // and nothing else, and the general one.  Folding the puts
-                // into the first body as a runtime check cost 7 % at 512^3;
-                // source code in the put body cost 5-11 % on 2x2x2 runs.
+                // and nothing else, partial tiles without puts, and the
+                // general one.  Folding the puts into the first body as a
+                // runtime check cost 7 % at 512^3; source code in the put
+                // body cost 5-11 % on 2x2x2 runs; partial tiles on the
+                // general body cost 16 % at 1200^3.
                 if (fast_ && !item_puts) z_loop<true, false>(z1 - z0);
                 else if (fast_ && nl_ == 0) z_loop<true, true>(z1 - z0);
+                else if (!item_puts) z_loop<false, false>(z1 - z0);
                 else z_loop<false, true>(z1 - z0);
                 end_item(it);
             }
