@@ -751,7 +751,7 @@ struct Step {
 
     // One compute plane z.  FAST: a whole tile (every row and point valid)
     // with no halo puts, sources or receivers.
-    template <int P, bool FAST, bool PUTS>
+    template <int P, bool FAST, bool PUTS, bool LOC>
     __device__ __forceinline__ void step_plane(int z)
     {
         // (1) x/y neighbours from the compute plane, staged R loads ago (its
@@ -801,7 +801,7 @@ struct Step {
         for (int r = 0; r < PY; ++r) laplacian_row<P>(yv, lf[r], rt[r], r, lap[r]);
         // sources and receivers: only on the planes that hold some (fast
         // items with puts have none)
-        const bool locz = !(FAST && PUTS) && z >= zloc_lo_ && z <= zloc_hi_;
+        const bool locz = LOC && z >= zloc_lo_ && z <= zloc_hi_;
         if (locz) add_sources(z, lap);
         // leapfrog update with the sponge
         G un[PY], wn[PY];
@@ -917,16 +917,16 @@ struct Step {
     }
 
     // the compute planes of one item, KP per trip of the loop
-    template <bool FAST, bool PUTS>
+    template <bool FAST, bool PUTS, bool LOC>
     __device__ __forceinline__ void z_loop(int nzc)
     {
 #pragma unroll 1
         for (int tb = 0; tb < nzc; tb += KP) {
-            step_plane<0, FAST, PUTS>(z0 + tb);
-            if (tb + 1 < nzc) step_plane<1, FAST, PUTS>(z0 + tb + 1);
+            step_plane<0, FAST, PUTS, LOC>(z0 + tb);
+            if (tb + 1 < nzc) step_plane<1, FAST, PUTS, LOC>(z0 + tb + 1);
             if constexpr (KP > 2) {
-                if (tb + 2 < nzc) step_plane<2, FAST, PUTS>(z0 + tb + 2);
-                if (tb + 3 < nzc) step_plane<3, FAST, PUTS>(z0 + tb + 3);
+                if (tb + 2 < nzc) step_plane<2, FAST, PUTS, LOC>(z0 + tb + 2);
+                if (tb + 3 < nzc) step_plane<3, FAST, PUTS, LOC>(z0 + tb + 3);
             }
             shift_queue();
         }
@@ -1009,17 +1009,21 @@ struct Step {
                 begin_item(it);
                 fill_one<0>(); fill_one<1>(); fill_one<2>(); fill_one<3>();
                 fill_one<4>(); fill_one<5>(); fill_one<6>(); fill_one<7>();
-                // four loop bodies: whole tiles without puts (sources and
-                // receivers handled on their planes), whole tiles with puts
-                // and nothing else, partial tiles without puts, and the
+                // five loop bodies, so that each item runs the smallest
+                // code that covers it (instruction fetch limits the loop):
+                // whole tiles with neither puts nor sources/receivers,
+                // whole tiles with sources/receivers on some planes, whole
+                // tiles with puts, partial tiles without puts, and the
                 // general one.  Folding the puts into the first body as a
                 // runtime check cost 7 % at 512^3; source code in the put
                 // body cost 5-11 % on 2x2x2 runs; partial tiles on the
-                // general body cost 16 % at 1200^3.
-                if (fast_ && !item_puts) z_loop<true, false>(z1 - z0);
-                else if (fast_ && nl_ == 0) z_loop<true, true>(z1 - z0);
-                else if (!item_puts) z_loop<false, false>(z1 - z0);
-                else z_loop<false, true>(z1 - z0);
+                // general body cost 16 % at 1200^3; the source/receiver
+                // code in the main body cost 7-9 % with 16-bit storage.
+                if (fast_ && !item_puts && nl_ == 0) z_loop<true, false, false>(z1 - z0);
+                else if (fast_ && !item_puts) z_loop<true, false, true>(z1 - z0);
+                else if (fast_ && nl_ == 0) z_loop<true, true, false>(z1 - z0);
+                else if (!item_puts) z_loop<false, false, true>(z1 - z0);
+                else z_loop<false, true, true>(z1 - z0);
                 end_item(it);
             }
             if (k + 1 < A.nk) {
