@@ -68,7 +68,9 @@ typedef uint64_t gw_gptr;         /* handle of a global allocation; 0 = none */
  * GW_F16S and GW_BF16, FP64 for GW_F64.  GW_F16S stores FP16 scaled by a
  * per-shot power of two; the reduced types use the delta form
  * w_n = u_n - G u_{n-1}:  w' = G (w + coef (lap(u) + src)),  u' = G u + w'
- * (algebraically the same recurrence; see the library's design notes). */
+ * (algebraically the same recurrence: u' = G u + G (u - G u_{n-1} +
+ * coef (lap + src)) = G (2u - G u_{n-1} + coef (lap + src)); only the
+ * rounding of the stored values differs). */
 enum { GW_F32 = 0, GW_F64 = 1, GW_F16S = 2, GW_BF16 = 3 };
 
 /* How the halo of each subdomain is refreshed after a step. */
