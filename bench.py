@@ -695,7 +695,7 @@ def run_minimod_size(steps=100, warmup=5, seed=2506, device=0):
             "tile": info["tile"], "items": info["items"]}
 
 
-def run_cannon(n=CANNON_N, p=CANNON_P, runs=3, cluster=2, group=16, bk=64,
+def run_cannon(n=CANNON_N, p=CANNON_P, runs=3, tile_m=256, group=4,
                seed=2506, device=0):
     """Cannon's ring exchange (section 5) on dyadic BF16 inputs: TFLOP/s of
     whole runs (P ring steps each, puts overlapped) and of the block-product
@@ -711,7 +711,7 @@ def run_cannon(n=CANNON_N, p=CANNON_P, runs=3, cluster=2, group=16, bk=64,
     with Segment(p * (per + (1 << 20)), nranks=p, device=device) as seg:
         cn = gw.gw_cannon_create(seg.ctx, n, p)
         try:
-            gw.gw_cannon_schedule(cn, cluster, group, bk)
+            gw.gw_cannon_schedule(cn, tile_m, group)
             gw.gw_cannon_set(cn, a_bits, bt_bits)
             del a_bits, bt_bits
             st = torch.cuda.current_stream()
@@ -738,7 +738,7 @@ def run_cannon(n=CANNON_N, p=CANNON_P, runs=3, cluster=2, group=16, bk=64,
     kms = k["gemm_ms"] / max(1, k["launches"])
     kflops = flops / p                            # one ring step
     return {
-        "n": n, "p": p, "cluster": cluster, "group": group, "bk": bk, "runs": runs,
+        "n": n, "p": p, "tile_m": tile_m, "group": group, "runs": runs,
         "inputs": "dyadic bf16",
         "ms_per_run": ms, "tflops": flops / (ms * 1e-3) / 1e12,
         "kernel_ms": kms, "kernel_launches_per_run": p, "grid": k["grid"],
@@ -875,21 +875,18 @@ def main():
     ap.add_argument("--cannon", type=int, default=0, metavar="N",
                     help="Cannon ring-exchange product of two N x N matrices")
     ap.add_argument("--cannon-p", type=int, default=CANNON_P, help="ring ranks")
-    ap.add_argument("--cannon-cluster", type=int, default=2,
-                    help="CTAs sharing a B tile (1 or 2)")
-    ap.add_argument("--cannon-group", type=int, default=16,
+    ap.add_argument("--cannon-tile-m", type=int, default=256,
+                    help="rows of a CTA's output tile (128 or 256)")
+    ap.add_argument("--cannon-group", type=int, default=4,
                     help="tile rows per raster group")
-    ap.add_argument("--cannon-bk", type=int, default=64,
-                    help="K depth of a pipeline stage (64 or 32)")
     args = ap.parse_args()
     if args.cannon:
         from paper_2506_02486_gb300 import buildlib
         buildlib.build()
         print(json.dumps({"cannon": run_cannon(args.cannon, args.cannon_p,
                                                runs=max(1, args.steps if args.steps != 1000 else 3),
-                                               cluster=args.cannon_cluster,
-                                               group=args.cannon_group,
-                                               bk=args.cannon_bk)}), flush=True)
+                                               tile_m=args.cannon_tile_m,
+                                               group=args.cannon_group)}), flush=True)
         return 0
     if args.batch:
         return run_batch_modes(args)

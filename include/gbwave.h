@@ -290,15 +290,14 @@ gw_status gw_cannon_set(gw_cannon *cn, const void *a, const void *bt,
  * GW_ERR_TIMEOUT by gw_cannon_sync / gw_cannon_read_c. */
 gw_status gw_cannon_run(gw_cannon *cn, gw_stream stream);
 /* Schedule of the block-product kernel (results are the same bits for
- * every choice).  cluster: CTAs per cluster over 128 x 256 tiles; 1 loads
- * every tile alone, 2 (default) pairs vertically adjacent tiles that share
- * each B tile through a TMA multicast, 4 takes a 2 x 2 block of tiles that
- * share A and B tiles.  group: tile rows per raster group (default 16), in
- * 1 .. 1024 and even for clusters 2 and 4; the CTAs running at the same
- * time sweep a group's rows column by column.  bk: K depth of one pipeline
- * stage, 64 (default: 4 stages of 48 KB) or 32 (9 stages of 24 KB).
- * GW_ERR_CUDA if the device cannot hold a cluster of that size. */
-gw_status gw_cannon_schedule(gw_cannon *cn, int cluster, int group, int bk);
+ * every choice; one CTA per output tile, no clusters).  tile_m: rows of a
+ * CTA's 256-column output tile, 256 (default: 3 pipeline stages of 64 KB,
+ * two M = 128 products per stage reading the same B tile) or 128 (4 stages
+ * of 48 KB, two accumulators so a tile's epilogue overlaps the next tile's
+ * products).  group: tile rows per raster group, 1 .. 1024 (default 4); the
+ * CTAs running at the same time sweep a group's rows column by column.
+ * GW_ERR_ARG for other values. */
+gw_status gw_cannon_schedule(gw_cannon *cn, int tile_m, int group);
 /* Device synchronisation and the kernel error word. */
 gw_status gw_cannon_sync(gw_cannon *cn);
 /* C (N x N, row-major FP32) to the host (on_device = 0) or the device,

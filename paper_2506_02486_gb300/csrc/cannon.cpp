@@ -26,12 +26,11 @@ struct gw_cannon {
     gw_gptr ga = 0, gb[2] = {0, 0}, gc = 0;
     int cur = 0;              // B buffer holding the current stripes
     int off = 0;              // rank r holds B column stripe (r + off) mod p
-    // [K box 64 or 32][A box 128 or 64 rows]; [buffer][K box][B box 256 or 128]
-    CUtensorMap map_a[2][2];
-    CUtensorMap map_b[2][2][2];
-    int cluster = 2;          // CTAs sharing one B tile (TMA multicast)
-    int bk = 64;              // K depth of a pipeline stage
-    int group = 16;           // tile rows per raster group
+    // A boxes of 128 and 256 rows; B boxes of 256 rows per buffer
+    CUtensorMap map_a[2];
+    CUtensorMap map_b[2];
+    int tile_m = 256;         // rows of one CTA's output tile (128 or 256)
+    int group = 4;            // tile rows per raster group
     unsigned *err = nullptr;  // device error word
     gw_gptr gerr = 0;
     bool timing = false;
@@ -60,9 +59,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder()
 }
 
 // {K, rows, rank} over the stripes of one symmetric BF16 allocation; box
-// bk (one swizzle row of 2 bk bytes) x box_rows x 1; rows and K beyond the
+// 64 (one 128-byte swizzle row) x box_rows x 1; rows and K beyond the
 // stripe read as zeros.
-gw_status encode_stripes(gw_cannon *cn, CUtensorMap *m, gw_gptr g, int bk, int box_rows)
+gw_status encode_stripes(gw_cannon *cn, CUtensorMap *m, gw_gptr g, int box_rows)
 {
     auto fn = encoder();
     if (!fn) return fail(GW_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
@@ -70,11 +69,11 @@ gw_status encode_stripes(gw_cannon *cn, CUtensorMap *m, gw_gptr g, int bk, int b
     GW_TRY(ctx_resolve(cn->ctx, g, 0, &base, nullptr));
     cuuint64_t dims[3] = {(cuuint64_t)cn->n, (cuuint64_t)cn->ns, (cuuint64_t)cn->p};
     cuuint64_t strides[2] = {(cuuint64_t)cn->n * 2, (cuuint64_t)cn->ctx->rank_bytes};
-    cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         return fail(GW_ERR_CUDA, "cuTensorMapEncodeTiled (stripes) failed (%d)", (int)r);
@@ -126,11 +125,8 @@ gw_status launch_step(gw_cannon *cn, cudaStream_t s, int skip_loads = 0,
     a.wait_ns = wait_ns;
     a.skip_loads = skip_loads;
     if (cn->timing) GW_TRY_CUDA(cudaEventRecord(cn->ev0, s));
-    // cluster 1: 1 x 1; 2: 2 x 1 (B tiles shared); 4: 2 x 2 (A and B shared)
-    const int ia = cn->cluster == 4 ? 1 : 0, ib = cn->cluster >= 2 ? 1 : 0;
-    const int ik = cn->bk == 64 ? 0 : 1;
-    GW_TRY_CUDA(launch_gemm_bf16(&cn->map_a[ik][ia], &cn->map_b[cn->cur][ik][ib], a,
-                                 cn->cluster, cn->bk, cn->grid, s));
+    GW_TRY_CUDA(launch_gemm_bf16(&cn->map_a[cn->tile_m == 256 ? 1 : 0], &cn->map_b[cn->cur],
+                                 a, cn->tile_m, cn->grid, s));
     if (cn->timing) {
         GW_TRY_CUDA(cudaEventRecord(cn->ev1, s));
         GW_TRY_CUDA(cudaEventSynchronize(cn->ev1));
@@ -142,19 +138,16 @@ gw_status launch_step(gw_cannon *cn, cudaStream_t s, int skip_loads = 0,
     return GW_OK;
 }
 
-// One resident CTA per SM (a multiple of the cluster size), never more CTAs
-// than tiles.
-gw_status set_grid(gw_cannon *cn, int cluster, int bk)
+// One resident CTA per SM, never more CTAs than tiles.
+gw_status set_grid(gw_cannon *cn, int tile_m)
 {
-    const int cm = cluster >= 2 ? 2 : 1, cnn = cluster / cm;
-    const int tm = (cn->ns + gemm_tile_m() - 1) / gemm_tile_m();
+    const int tm = (cn->ns + tile_m - 1) / tile_m;
     const int tn = (cn->ns + gemm_tile_n() - 1) / gemm_tile_n();
-    const int units = cn->p * ((tm + cm - 1) / cm) * ((tn + cnn - 1) / cnn);
-    const int most = gemm_max_ctas(cluster, bk, cn->ctx->num_sms);
-    if (most < cluster) return fail(GW_ERR_CUDA, "no resident cluster of %d CTAs", cluster);
-    cn->cluster = cluster;
-    cn->bk = bk;
-    cn->grid = std::min(most, units * cluster);
+    const int tiles = cn->p * tm * tn;
+    const int most = gemm_max_ctas(tile_m, cn->ctx->num_sms);
+    if (most < 1) return fail(GW_ERR_CUDA, "the block-product kernel cannot be resident");
+    cn->tile_m = tile_m;
+    cn->grid = std::min(most, tiles);
     return GW_OK;
 }
 
@@ -212,35 +205,27 @@ gw_status gw_cannon_create(gw_ctx *c, int n, int p, gw_cannon **out)
     cn->err = reinterpret_cast<unsigned *>(errp);
     if (cudaMemset(cn->err, 0, sizeof(unsigned)) != cudaSuccess)
         return cleanup(fail(GW_ERR_CUDA, "error word"));
-    for (int k = 0; k < 2 && st == GW_OK; ++k)
-        for (int h = 0; h < 2 && st == GW_OK; ++h)
-            st = encode_stripes(cn, &cn->map_a[k][h], cn->ga, 64 >> k, gemm_tile_m() >> h);
+    for (int h = 0; h < 2 && st == GW_OK; ++h)
+        st = encode_stripes(cn, &cn->map_a[h], cn->ga, 128 << h);
     for (int b = 0; b < 2 && st == GW_OK; ++b)
-        for (int k = 0; k < 2 && st == GW_OK; ++k)
-            for (int h = 0; h < 2 && st == GW_OK; ++h)
-                st = encode_stripes(cn, &cn->map_b[b][k][h], cn->gb[b], 64 >> k,
-                                    gemm_tile_n() >> h);
+        st = encode_stripes(cn, &cn->map_b[b], cn->gb[b], gemm_tile_n());
     if (st != GW_OK) return cleanup(st);
     if (cudaEventCreate(&cn->ev0) != cudaSuccess || cudaEventCreate(&cn->ev1) != cudaSuccess)
         return cleanup(fail(GW_ERR_CUDA, "events"));
-    st = set_grid(cn, 2, 64);
+    st = set_grid(cn, 256);
     if (st != GW_OK) return cleanup(st);
     *out = cn;
     return GW_OK;
 }
 
-gw_status gw_cannon_schedule(gw_cannon *cn, int cluster, int group, int bk)
+gw_status gw_cannon_schedule(gw_cannon *cn, int tile_m, int group)
 {
     if (!cn) return fail(GW_ERR_ARG, "NULL argument");
-    if (cluster != 1 && cluster != 2 && cluster != 4)
-        return fail(GW_ERR_ARG, "cluster size must be 1, 2 or 4");
-    const int cm = cluster >= 2 ? 2 : 1;
-    if (group < cm || group > 1024 || group % cm)
-        return fail(GW_ERR_ARG, "group must be a multiple of the cluster's tile rows in 1 .. 1024");
+    if (tile_m != 128 && tile_m != 256) return fail(GW_ERR_ARG, "tile rows must be 128 or 256");
+    if (group < 1 || group > 1024) return fail(GW_ERR_ARG, "group must be in 1 .. 1024");
     std::lock_guard<std::recursive_mutex> lk(cn->ctx->mu);
     GW_TRY_CUDA(cudaSetDevice(cn->ctx->device));
-    if (bk != 64 && bk != 32) return fail(GW_ERR_ARG, "stage depth must be 64 or 32");
-    GW_TRY(set_grid(cn, cluster, bk));
+    GW_TRY(set_grid(cn, tile_m));
     cn->group = group;
     return GW_OK;
 }

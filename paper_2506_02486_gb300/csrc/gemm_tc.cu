@@ -2,13 +2,20 @@
 // multiplication): C_q = A_q * B_q^T for a set of problems q, BF16 operands,
 // FP32 accumulation, on the 5th-generation tensor cores.
 //
-// One persistent CTA per SM, six warps:
-//   warp 0      TMA producer: 128 x 64 A and 256 x 64 B tiles (K-major,
-//               128-byte swizzle) into a 4-stage shared-memory ring;
-//   warp 1      allocates 512 tensor-memory columns (two 128 x 256 FP32
-//               accumulators) and issues tcgen05.mma (M 128, N 256, K 16);
-//   warps 2-5   epilogue: tensor memory -> registers -> C, while the MMA
-//               warp fills the other accumulator.
+// One persistent CTA per SM, six warps, one CTA per output tile (no
+// clusters):
+//   warp 0      TMA producer: (128 MH) x 64 A and 256 x 64 B tiles
+//               (K-major, 128-byte swizzle) into a ring of shared-memory
+//               stages;
+//   warp 1      allocates 512 tensor-memory columns and issues tcgen05.mma
+//               (M 128, N 256, K 16), MH products per K slice, all reading
+//               the same B stage;
+//   warps 2-5   epilogue: tensor memory -> registers -> C.
+// MH = 1: 128 x 256 tiles, 4 stages of 48 KB, two accumulators, so the
+// epilogue of one tile runs while the next tile is multiplied.  MH = 2:
+// 256 x 256 tiles, 3 stages of 64 KB, one pair of accumulators (the two
+// M halves); a K step then brings 64 KB from L2 for twice the products,
+// 128 instead of 85 multiply-adds per operand byte.
 // Every wait is bounded; a wait that gives up latches ERRB_TIMEOUT, the CTA
 // drains what it has in flight (bounded), frees its tensor memory and leaves.
 #include <cuda.h>
@@ -22,36 +29,28 @@
 namespace gw {
 namespace {
 
-constexpr int BM = 128, BN = 256;
+constexpr int BH = 128, BN = 256, BK = 64;     // M half, N, K depth of a stage
 constexpr int THREADS = 192;
-constexpr uint32_t TMEM_COLS = 2 * BN;          // two accumulators
+constexpr uint32_t TMEM_COLS = 2 * BN;         // 512: the whole tensor memory
 
-// Stage shape for a K depth of BK BF16 per stage: 64 (128-byte rows,
-// 128-byte swizzle, 4 stages of 48 KB) or 32 (64-byte rows, 64-byte
-// swizzle, 9 stages of 24 KB: the same bytes in flight, refilled in finer
-// steps, so the loads run further ahead of the MMAs).
-template <int BK_>
+template <int MH_>
 struct Shape {
-    static constexpr int BK = BK_;
-    static constexpr int STAGES = BK == 64 ? 4 : 9;
-    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int MH = MH_;
+    static constexpr int BMT = BH * MH;                  // tile rows
+    static constexpr int STAGES = MH == 1 ? 4 : 3;
+    static constexpr int NACC = MH == 1 ? 2 : 1;         // accumulator sets
+    static constexpr int A_BYTES = BMT * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    // barriers: full[S], empty[S], tfull[2], tempty[2], drain; then the
-    // TMEM base address and an abort flag
+    // barriers: full[S], empty[S], tfull[NACC], tempty[NACC], drain; then
+    // the TMEM base address and an abort flag
     static constexpr int OFF_BAR = STAGES * STAGE_BYTES;
-    static constexpr int NBAR = 2 * STAGES + 5;
+    static constexpr int NBAR = 2 * STAGES + 2 * NACC + 1;
     static constexpr int OFF_TMEM = OFF_BAR + 8 * NBAR;
     static constexpr int SMEM_BYTES = OFF_TMEM + 16 + 1024;   // + ring alignment
     static_assert(SMEM_BYTES <= 232448, "shared memory");
+    static_assert(NACC * MH * BN == (int)TMEM_COLS, "tensor memory");
 };
-
-// Operand descriptor of a K-major tile of rows of BK BF16 (see tc_ptx.cuh).
-template <int BK>
-__device__ __forceinline__ uint64_t sdesc(const void *tile)
-{
-    return BK == 64 ? tc::sdesc_k128(tile) : tc::sdesc_k64(tile);
-}
 
 struct TileCoord {
     int q, tm, tn;
@@ -109,61 +108,40 @@ __device__ __forceinline__ void give_up(volatile int *abortf, unsigned *err)
     *abortf = 1;
 }
 
-// Clusters of CM x CN CTAs on a CM x CN block of tiles (CTA rank
-// ci + CM * cj takes tile row tm0 + ci, tile column tn0 + cj).  The CN CTAs
-// of a tile row share its A tile and the CM CTAs of a tile column its B
-// tile: each CTA loads 1/CN of its A tile and 1/CM of its B tile and
-// multicasts them to the CTAs sharing them, so with 2 x 1 a CTA fetches
-// 32 KB per K step from L2 and with 2 x 2 24 KB instead of 48 KB.  A stage
-// may only be refilled once every CTA that writes into it is done with it:
-// each MMA warp's commit arrives on the empty barrier of itself and of the
-// CTAs that share its tiles (count CM + CN - 1).
-template <int CM, int CN, int BK_>
+// Tile t of the launch is tile_of(t) (problems one after another, groups
+// of `group` tile rows swept column by column); CTA b takes tiles
+// b, b + grid, ....  Accumulator set of a CTA's local tile l: l % NACC,
+// used for the (l / NACC)-th time.
+template <int MH>
 __global__ void __launch_bounds__(THREADS, 1)
 k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
             const __grid_constant__ CUtensorMap map_b,
             const __grid_constant__ GemmArgs A)
 {
-    using SH = Shape<BK_>;
-    constexpr int BK = SH::BK, STAGES = SH::STAGES, A_BYTES = SH::A_BYTES,
-                  B_BYTES = SH::B_BYTES, STAGE_BYTES = SH::STAGE_BYTES;
+    using SH = Shape<MH>;
+    constexpr int STAGES = SH::STAGES, NACC = SH::NACC, BMT = SH::BMT,
+                  A_BYTES = SH::A_BYTES, STAGE_BYTES = SH::STAGE_BYTES;
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte alignment: the swizzle pattern repeats every 8 rows of 128 B
-    // (the same offset in every CTA, as multicast requires)
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SH::OFF_BAR);
     uint64_t *full = bars, *empty = bars + STAGES;
-    uint64_t *tfull = bars + 2 * STAGES, *tempty = tfull + 2, *drain = tempty + 2;
+    uint64_t *tfull = bars + 2 * STAGES, *tempty = tfull + NACC, *drain = tempty + NACC;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SH::OFF_TMEM);
     volatile int *abortf = reinterpret_cast<volatile int *>(smem + SH::OFF_TMEM + 4);
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int CL = CM * CN;
-    const int crank = CL > 1 ? (int)tc::cluster_ctarank() : 0;
-    const int ci = crank % CM, cj = crank / CM;
-    const int unit0 = CL > 1 ? (int)tc::cluster_id_x() : (int)blockIdx.x;
-    const int nunit_step = CL > 1 ? (int)tc::ncluster_x() : (int)gridDim.x;
-    const int tmc = (A.m + BM - 1) / BM, tnc = (A.n + BN - 1) / BN;
-    const int tmu = (tmc + CM - 1) / CM;          // unit rows
-    const int tnu = (tnc + CN - 1) / CN;          // unit columns
-    const int nunits = A.nprob * tmu * tnu;
+    const int tmc = (A.m + BMT - 1) / BMT, tnc = (A.n + BN - 1) / BN;
+    const int ntiles = A.nprob * tmc * tnc;
     const int nkb = (A.k + BK - 1) / BK;
-    const int group_u = max(1, A.group / CM);     // unit rows per raster group
-    // CTAs sharing this CTA's A tile (same ci) and its B tile (same cj)
-    uint16_t row_peers = 0, col_peers = 0;
-#pragma unroll
-    for (int j = 0; j < CN; ++j) row_peers |= (uint16_t)(1u << (ci + CM * j));
-#pragma unroll
-    for (int i = 0; i < CM; ++i) col_peers |= (uint16_t)(1u << (i + CM * cj));
-    const uint16_t writers = row_peers | col_peers;
+    const int group = max(1, A.group);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CM + CN - 1);   // one commit per writer
+            mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NACC; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 4);        // one arrival per epilogue warp
         }
@@ -177,7 +155,6 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (CL > 1) tc::cluster_sync();          // peers' barriers exist
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
@@ -187,9 +164,8 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
             const uint64_t pol = policy_evict_normal();
             uint32_t it = 0;
             // (the self-test issues no loads, so that the waits run out)
-            for (int u = unit0; u < nunits && !A.skip_loads; u += nunit_step) {
-                const TileCoord tc_ = tile_of(u, tmu, tnu, group_u);
-                const int tm = tc_.tm * CM + ci, tn = tc_.tn * CN + cj;
+            for (int t = blockIdx.x; t < ntiles && !A.skip_loads; t += gridDim.x) {
+                const TileCoord tc_ = tile_of(t, tmc, tnc, group);
                 const int ra = A.a_rank[tc_.q], rb = A.b_rank[tc_.q];
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const uint32_t s = it % STAGES;
@@ -200,18 +176,8 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
                     }
                     unsigned char *st = smem + s * STAGE_BYTES;
                     mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                    if (CN == 1)
-                        tma_load_3d(st, &map_a, &full[s], kb * BK, tm * BM, ra, pol);
-                    else
-                        tc::tma_load_3d_mc(st + cj * (A_BYTES / CN), &map_a, &full[s],
-                                           kb * BK, tm * BM + cj * (BM / CN), ra,
-                                           row_peers, pol);
-                    if (CM == 1)
-                        tma_load_3d(st + A_BYTES, &map_b, &full[s], kb * BK, tn * BN, rb, pol);
-                    else
-                        tc::tma_load_3d_mc(st + A_BYTES + ci * (B_BYTES / CM), &map_b,
-                                           &full[s], kb * BK, tn * BN + ci * (BN / CM), rb,
-                                           col_peers, pol);
+                    tma_load_3d(st, &map_a, &full[s], kb * BK, tc_.tm * BMT, ra, pol);
+                    tma_load_3d(st + A_BYTES, &map_b, &full[s], kb * BK, tc_.tn * BN, rb, pol);
                 }
             }
         produced:
@@ -222,16 +188,15 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(BH, BN);
             uint32_t it = 0, local = 0;
-            for (int u = unit0; u < nunits; u += nunit_step, ++local) {
-                const uint32_t b = local & 1u;
-                if (local >= 2 && !bwait(&tempty[b], ((local >> 1) - 1) & 1u, abortf, A.wait_ns)) {
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+                const uint32_t b = local % NACC, use = local / NACC;
+                if (use >= 1 && !bwait(&tempty[b], (use - 1) & 1u, abortf, A.wait_ns)) {
                     give_up(abortf, A.err);
                     break;
                 }
                 tc::fence_after_sync();
-                const uint32_t d = tmem + b * BN;
                 bool ok = true;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const uint32_t s = it % STAGES;
@@ -242,18 +207,22 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
                     }
                     tc::fence_after_sync();
                     const unsigned char *st = smem + s * STAGE_BYTES;
-                    const uint64_t ad = sdesc<BK>(st);
-                    const uint64_t bd = sdesc<BK>(st + A_BYTES);
+                    const uint64_t bd = tc::sdesc_k128(st + A_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk)   // 32 bytes along K each
-                        tc::mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc,
-                                     (kb | kk) != 0);
-                    // stage free (in every CTA that wrote into it) when done
-                    if (CL == 1) tc::commit(&empty[s]);
-                    else tc::commit_mc(&empty[s], writers);
+                    for (int h = 0; h < MH; ++h) {
+                        // M half h: rows 128 h .. of the A stage (16 KB, a
+                        // whole number of 1024-byte swizzle atoms further)
+                        const uint64_t ad = tc::sdesc_k128(st + h * (BH * BK * 2));
+                        const uint32_t d = tmem + (b * MH + h) * BN;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk)   // 32 bytes along K each
+                            tc::mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc,
+                                         (kb | kk) != 0);
+                    }
+                    tc::commit(&empty[s]);                 // stage free when done
                 }
                 if (!ok) break;
-                tc::commit(&tfull[b]);                     // accumulator ready
+                tc::commit(&tfull[b]);                     // accumulators ready
             }
             // no MMA may still be running when the CTA leaves
             tc::commit(drain);
@@ -262,36 +231,40 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
     } else {
         // ---------------- epilogue (warps 2..5) ----------------
         const int lg = warp & 3;                  // TMEM lane group of this warp
-        const int row_in_tile = 32 * lg + lane;
+        const int row_in_half = 32 * lg + lane;
         uint32_t local = 0;
-        for (int u = unit0; u < nunits; u += nunit_step, ++local) {
-            const uint32_t b = local & 1u;
-            if (!bwait(&tfull[b], (local >> 1) & 1u, abortf, A.wait_ns)) {
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+            const uint32_t b = local % NACC, use = local / NACC;
+            if (!bwait(&tfull[b], use & 1u, abortf, A.wait_ns)) {
                 give_up(abortf, A.err);
                 break;
             }
             tc::fence_after_sync();
-            const TileCoord tc_ = tile_of(u, tmu, tnu, group_u);
-            const int row = (tc_.tm * CM + ci) * BM + row_in_tile;
-            const int col0 = (tc_.tn * CN + cj) * BN;
-            float *crow = A.c + A.c_off[tc_.q] + (long long)row * A.ldc + col0;
-            const bool vec = ((reinterpret_cast<uintptr_t>(crow) & 15u) == 0);
+            const TileCoord tc_ = tile_of(t, tmc, tnc, group);
+            const int col0 = tc_.tn * BN;
 #pragma unroll 1
-            for (int ch = 0; ch < BN / 32; ++ch) {
-                float v[32];
-                tc::ld_32cols(tmem + ((uint32_t)(32 * lg) << 16) + b * BN + ch * 32, v);
-                if (row >= A.m) continue;
-                const int c0 = col0 + ch * 32;
-                float *p = crow + ch * 32;
-                if (vec && c0 + 32 <= A.n) {
+            for (int h = 0; h < MH; ++h) {
+                const int row = tc_.tm * BMT + h * BH + row_in_half;
+                float *crow = A.c + A.c_off[tc_.q] + (long long)row * A.ldc + col0;
+                const bool vec = ((reinterpret_cast<uintptr_t>(crow) & 15u) == 0);
+                const uint32_t tcol = tmem + ((uint32_t)(32 * lg) << 16) + (b * MH + h) * BN;
+#pragma unroll 1
+                for (int ch = 0; ch < BN / 32; ++ch) {
+                    float v[32];
+                    tc::ld_32cols(tcol + ch * 32, v);     // whole warp, every row
+                    if (row >= A.m) continue;
+                    const int c0 = col0 + ch * 32;
+                    float *p = crow + ch * 32;
+                    if (vec && c0 + 32 <= A.n) {
 #pragma unroll
-                    for (int i = 0; i < 32; i += 4)
-                        *reinterpret_cast<float4 *>(p + i) =
-                            make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-                } else {
+                        for (int i = 0; i < 32; i += 4)
+                            *reinterpret_cast<float4 *>(p + i) =
+                                make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                    } else {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (c0 + i < A.n) p[i] = v[i];
+                        for (int i = 0; i < 32; ++i)
+                            if (c0 + i < A.n) p[i] = v[i];
+                    }
                 }
             }
             tc::fence_before_sync();
@@ -302,99 +275,65 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap map_a,
 
     tc::fence_before_sync();
     __syncthreads();
-    // a peer may still multicast into this CTA or arrive on its barriers
-    // until it has drained its own copies and MMAs
-    if (CL > 1) tc::cluster_sync();
     tc::fence_after_sync();
     if (warp == 1) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
 
 }  // namespace
 
-int gemm_tile_m() { return BM; }
 int gemm_tile_n() { return BN; }
 
-template <int CM, int CN, int BK>
+template <int MH>
 static cudaError_t set_attr()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16<CM, CN, BK>,
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16<MH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Shape<BK>::SMEM_BYTES);
+                                         Shape<MH>::SMEM_BYTES);
     done = e == cudaSuccess;
     return e;
 }
 
-static cudaLaunchConfig_t config(int cl, int grid, int smem, cudaStream_t s,
-                                 cudaLaunchAttribute *attr)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cl;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cfg;
-}
-
-template <int CM, int CN, int BK>
+template <int MH>
 static int max_ctas(int num_sms)
 {
-    constexpr int CL = CM * CN;
-    if (set_attr<CM, CN, BK>() != cudaSuccess) return 0;
-    if (CL == 1) return num_sms;
-    cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = config(CL, CL * (num_sms / CL), Shape<BK>::SMEM_BYTES, nullptr, attr);
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_gemm_bf16<CM, CN, BK>, &cfg) != cudaSuccess)
+    if (set_attr<MH>() != cudaSuccess) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemm_bf16<MH>, THREADS,
+                                                      Shape<MH>::SMEM_BYTES) != cudaSuccess)
         return 0;
-    return CL * n;
+    return per_sm >= 1 ? num_sms : 0;   // one CTA per SM: it holds all TMEM
 }
 
-template <int CM, int CN, int BK>
+template <int MH>
 static cudaError_t launch(const CUtensorMap &ma, const CUtensorMap &mb, const GemmArgs &a,
                           int grid, cudaStream_t s)
 {
-    cudaError_t e = set_attr<CM, CN, BK>();
+    cudaError_t e = set_attr<MH>();
     if (e != cudaSuccess) return e;
-    cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = config(CM * CN, grid, Shape<BK>::SMEM_BYTES, s, attr);
-    return cudaLaunchKernelEx(&cfg, k_gemm_bf16<CM, CN, BK>, ma, mb, a);
+    k_gemm_bf16<MH><<<grid, THREADS, Shape<MH>::SMEM_BYTES, s>>>(ma, mb, a);
+    return cudaGetLastError();
 }
 
-int gemm_max_ctas(int cluster, int bk, int num_sms)
+int gemm_max_ctas(int tile_m, int num_sms)
 {
-    const int key = cluster * 100 + bk;
-    switch (key) {
-    case 164: return max_ctas<1, 1, 64>(num_sms);
-    case 264: return max_ctas<2, 1, 64>(num_sms);
-    case 464: return max_ctas<2, 2, 64>(num_sms);
-    case 132: return max_ctas<1, 1, 32>(num_sms);
-    case 232: return max_ctas<2, 1, 32>(num_sms);
-    case 432: return max_ctas<2, 2, 32>(num_sms);
+    switch (tile_m) {
+    case 128: return max_ctas<1>(num_sms);
+    case 256: return max_ctas<2>(num_sms);
     default: return 0;
     }
 }
 
 cudaError_t launch_gemm_bf16(const void *map_a, const void *map_b, const GemmArgs &a,
-                             int cluster, int bk, int grid, cudaStream_t s)
+                             int tile_m, int grid, cudaStream_t s)
 {
     CUtensorMap ma, mb;
     memcpy(&ma, map_a, sizeof ma);
     memcpy(&mb, map_b, sizeof mb);
-    switch (cluster * 100 + bk) {
-    case 164: return launch<1, 1, 64>(ma, mb, a, grid, s);
-    case 264: return launch<2, 1, 64>(ma, mb, a, grid, s);
-    case 464: return launch<2, 2, 64>(ma, mb, a, grid, s);
-    case 132: return launch<1, 1, 32>(ma, mb, a, grid, s);
-    case 232: return launch<2, 1, 32>(ma, mb, a, grid, s);
-    case 432: return launch<2, 2, 32>(ma, mb, a, grid, s);
+    switch (tile_m) {
+    case 128: return launch<1>(ma, mb, a, grid, s);
+    case 256: return launch<2>(ma, mb, a, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -114,8 +114,9 @@ constexpr unsigned long long kWaitLimitNsHost = 4000000000ull;
 
 // C_q = A_q B_q^T for up to kGemmMaxProb problems of one shape: A_q is an
 // m x k BF16 stripe and B_q an n x k BF16 stripe (both K contiguous), read
-// through 3-D tensor maps {k, rows, rank} (128-byte swizzle; boxes 64 x 128
-// for A, 64 x 256 for B); C_q is m x n FP32 at c + c_off[q], row pitch ldc.
+// through 3-D tensor maps {k, rows, rank} (128-byte swizzle; boxes 64 x
+// tile_m for A, 64 x 256 for B); C_q is m x n FP32 at c + c_off[q], row
+// pitch ldc.
 constexpr int kGemmMaxProb = 64;
 struct GemmArgs {
     int nprob;
@@ -125,23 +126,20 @@ struct GemmArgs {
     long long c_off[kGemmMaxProb];  // element offset of its block in c
     float *c;
     long long ldc;
-    int group;                      // tile rows per raster group (multiple of the cluster size)
+    int group;                      // tile rows per raster group
     unsigned *err;                  // ERRB_TIMEOUT when a wait gave up
     unsigned long long wait_ns;     // bound of every wait (kWaitLimitNs normally)
     int skip_loads;                 // self-test: issue no loads, so the waits run out
 };
-int gemm_tile_m();
 int gemm_tile_n();
-// Clusters: 1 (one CTA per tile), 2 (2 x 1 tiles sharing B tiles), 4 (2 x 2
-// tiles sharing A and B tiles).  bk: K depth of a pipeline stage, 64 (4
-// stages, 128-byte swizzle) or 32 (9 stages, 64-byte swizzle).  Most CTAs
-// resident at once (a multiple of the cluster size); 0 on error.
-int gemm_max_ctas(int cluster, int bk, int num_sms);
+// tile_m: rows of one CTA's output tile, 128 (4 stages of 48 KB, two
+// accumulators) or 256 (3 stages of 64 KB, one accumulator pair).  Most
+// CTAs resident at once (one per SM); 0 on error.
+int gemm_max_ctas(int tile_m, int num_sms);
 // map_a / map_b: host copies of the encoded tensor maps (CUtensorMap) with
-// a box of bk elements along K (swizzle 2 bk bytes) and 128 A rows (64 with
-// cluster 4) or 256 B rows (128 with clusters 2 and 4).  grid: CTAs, a
-// multiple of the cluster size.
+// a box of 64 elements along K and tile_m A rows or 256 B rows.  grid:
+// CTAs, at most gemm_max_ctas.
 cudaError_t launch_gemm_bf16(const void *map_a, const void *map_b, const GemmArgs &a,
-                             int cluster, int bk, int grid, cudaStream_t s);
+                             int tile_m, int grid, cudaStream_t s);
 
 }  // namespace gw

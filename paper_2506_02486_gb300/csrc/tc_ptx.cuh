@@ -1,6 +1,7 @@
 // tc_ptx.cuh -- inline PTX for the 5th-generation tensor cores of sm_103a:
 // tensor-memory allocation, tcgen05.mma with shared-memory operand
-// descriptors, commits to mbarriers and tensor-memory loads.
+// descriptors, commits to this CTA's mbarriers and tensor-memory loads
+// (single-CTA forms only: cta_group::1, no clusters).
 #pragma once
 #include <stdint.h>
 
@@ -52,16 +53,6 @@ __device__ __forceinline__ uint64_t sdesc_k128(const void *tile)
            (1ull << 46) | (2ull << 61);
 }
 
-// The same for rows of 64 bytes (32 BF16 along K) written with 64-byte
-// swizzling: 8-row atoms of 512 bytes (stride byte offset 512), swizzle
-// mode 4 (64 B).
-__device__ __forceinline__ uint64_t sdesc_k64(const void *tile)
-{
-    const uint64_t a = smem_addr(tile);
-    return ((a >> 4) & 0x3FFFull) | (1ull << 16) | ((512ull >> 4) << 32) |
-           (1ull << 46) | (4ull << 61);
-}
-
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
 // both operands K-major: D format bits 4-5 = 1 (F32), A format bits 7-9 =
 // 1 (BF16), B format bits 10-12 = 1 (BF16), N / 8 in bits 17-22, M / 16 in
@@ -93,59 +84,6 @@ __device__ __forceinline__ void commit(uint64_t *bar)
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
         :: "r"(smem_addr(bar)) : "memory");
-}
-
-// The same arrival on the barrier at this offset in every CTA of the
-// cluster named in `mask`.
-__device__ __forceinline__ void commit_mc(uint64_t *bar, uint16_t mask)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster"
-        ".multicast::cluster.b64 [%0], %1;"
-        :: "r"(smem_addr(bar)), "h"(mask) : "memory");
-}
-
-// ---- clusters --------------------------------------------------------------
-
-__device__ __forceinline__ uint32_t cluster_ctarank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t cluster_id_x()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t ncluster_x()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-    return r;
-}
-// All threads of all CTAs of the cluster.
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
-                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// 3-D tiled TMA load of one box written to the same shared-memory offset in
-// every CTA of the cluster named in `mask`, each completing on its own
-// barrier at the offset of `bar`.
-__device__ __forceinline__ void tma_load_3d_mc(void *dst, const void *map, uint64_t *bar,
-                                               int c0, int c1, int c2, uint16_t mask,
-                                               uint64_t policy)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile"
-        ".mbarrier::complete_tx::bytes.multicast::cluster.L2::cache_hint"
-        " [%0], [%1, {%2, %3, %4}], [%5], %6, %7;"
-        :: "r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)),
-           "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar)), "h"(mask), "l"(policy)
-        : "memory");
 }
 
 // 32 consecutive FP32 columns of this thread's TMEM lane (32x32b shape: the

@@ -149,7 +149,7 @@ _SIGS = {
     "gw_cannon_set": [_P, _P, _P, _I],
     "gw_cannon_run": [_P, _P],
     "gw_cannon_sync": [_P],
-    "gw_cannon_schedule": [_P, _I, _I, _I],
+    "gw_cannon_schedule": [_P, _I, _I],
     "gw_cannon_read_c": [_P, _P, _I],
     "gw_cannon_timing": [_P, _I],
     "gw_cannon_selftest_timeout": [_P, ctypes.c_uint, ctypes.POINTER(_I)],
@@ -428,8 +428,8 @@ def gw_cannon_run(cn: int, stream=None):
     _check(lib().gw_cannon_run(cn, _stream(stream)), "gw_cannon_run")
 
 
-def gw_cannon_schedule(cn: int, cluster: int = 2, group: int = 16, bk: int = 64):
-    _check(lib().gw_cannon_schedule(cn, int(cluster), int(group), int(bk)),
+def gw_cannon_schedule(cn: int, tile_m: int = 256, group: int = 4):
+    _check(lib().gw_cannon_schedule(cn, int(tile_m), int(group)),
            "gw_cannon_schedule")
 
 

@@ -16,14 +16,13 @@ from workloads import matmul as mm
 pytestmark = pytest.mark.gpu
 
 
-def cannon_gpu(a_bits, bt_bits, n, p, runs=1, stats=False, cluster=2, group=16,
-               bk=64):
+def cannon_gpu(a_bits, bt_bits, n, p, runs=1, stats=False, tile_m=256, group=4):
     ensure_built()
     per = gw.gw_cannon_bytes(n, p)
     with Segment(p * (per + (1 << 20)), nranks=p) as seg:
         cn = gw.gw_cannon_create(seg.ctx, n, p)
         try:
-            gw.gw_cannon_schedule(cn, cluster, group, bk)
+            gw.gw_cannon_schedule(cn, tile_m, group)
             gw.gw_cannon_set(cn, a_bits, bt_bits)
             out = []
             for _ in range(runs):
@@ -37,18 +36,18 @@ def cannon_gpu(a_bits, bt_bits, n, p, runs=1, stats=False, cluster=2, group=16,
     return (out, pool) if stats else out
 
 
-@pytest.mark.parametrize("cluster,bk", [(1, 64), (2, 64), (4, 64), (1, 32),
-                                        (2, 32)])
+@pytest.mark.parametrize("tile_m", [256, 128])
 @pytest.mark.parametrize("n,p", [(256, 2), (328, 4), (384, 3), (512, 1),
-                                 (1152, 3)])
-def test_dyadic_inputs_bit_exact(n, p, cluster, bk):
+                                 (1152, 3), (1800, 2)])
+def test_dyadic_inputs_bit_exact(n, p, tile_m):
     """Ragged cases: 328 / 4 = 82 rows per stripe (one partial tile) and a
-    K tail of 8; 1152 / 3 = 384 = 3 tile rows (an odd count: the second CTA
-    of a cluster gets an empty tile; with 2 x 2 clusters also an odd count
-    of tile columns)."""
+    K tail of 8; 1152 / 3 = 384 rows (one and a half 256-row tiles, three
+    128-row tiles); 1800 / 2 = 900 rows and columns (3.5 tiles of 256 each
+    way, 7.03 of 128) with a K tail of 8: more tiles than one CTA per SM
+    when P = 2 at 128 rows."""
     a_bits, bt_bits, a, b = mm.pair(n, 100 + n + p, "dyadic")
     ref, _ = oc.cannon(a, b, p)
-    (c,) = cannon_gpu(a_bits, bt_bits, n, p, cluster=cluster, bk=bk)
+    (c,) = cannon_gpu(a_bits, bt_bits, n, p, tile_m=tile_m)
     assert np.array_equal(c.astype(np.float64), ref)
 
 
@@ -66,19 +65,17 @@ def test_uniform_inputs_within_fp32_bound():
 
 def test_ring_gives_the_bits_of_the_single_product():
     """Each element's sum runs over the same K blocks in the same order
-    whatever the stripe, tile or cluster it falls in."""
+    whatever the stripe, tile shape or raster group it falls in."""
     n = 768
     a_bits, bt_bits, _, _ = mm.pair(n, 17, "uniform")
-    (one,) = cannon_gpu(a_bits, bt_bits, n, 1, cluster=1)
+    (one,) = cannon_gpu(a_bits, bt_bits, n, 1, tile_m=128)
     for p in (1, 2, 3, 4, 6):
         (c,) = cannon_gpu(a_bits, bt_bits, n, p)
         assert np.array_equal(c, one), p
-    for cluster, group, bk in ((1, 1, 64), (2, 2, 64), (1, 3, 64), (2, 64, 64),
-                               (4, 2, 64), (4, 16, 64), (2, 16, 32), (1, 8, 32),
-                               (4, 16, 32)):
-        (c,) = cannon_gpu(a_bits, bt_bits, n, 2, cluster=cluster, group=group,
-                          bk=bk)
-        assert np.array_equal(c, one), (cluster, group, bk)
+    for tile_m, group in ((128, 1), (256, 1), (128, 3), (256, 2), (128, 64),
+                          (256, 16), (256, 1024)):
+        (c,) = cannon_gpu(a_bits, bt_bits, n, 2, tile_m=tile_m, group=group)
+        assert np.array_equal(c, one), (tile_m, group)
 
 
 def test_repeated_runs_and_pool_use():
@@ -105,8 +102,7 @@ def test_arguments_checked():
             gw.gw_cannon_create(seg.ctx, 100, 2)  # rows not 16-byte multiples
         cn = gw.gw_cannon_create(seg.ctx, 96, 2)
         try:
-            for bad in ((3, 16, 64), (2, 3, 64), (4, 0, 64), (1, 2000, 64),
-                        (2, 16, 48)):
+            for bad in ((64, 8), (192, 8), (256, 0), (128, 2000), (512, 8)):
                 with pytest.raises(gw.GWError):
                     gw.gw_cannon_schedule(cn, *bad)
         finally:
@@ -117,8 +113,8 @@ def test_paper_size_sampled_entries_exact():
     """The paper's 30240 x 30240 product on 4 ring ranks, the launch
     configuration the benchmark times: sampled entries against the oracle's
     one-by-one FP64 sums (exact for dyadic inputs), plus the entries of the
-    last rows and columns (ragged tiles: 7560 = 59 x 128 + 8 rows per stripe,
-    30240 = 118 x 256 + 32 columns)."""
+    last rows and columns (ragged tiles: 7560 = 29 x 256 + 136 rows and
+    columns per stripe block)."""
     n, p = 30240, 4
     ka = mm.dyadic_codes(n, n, 2506)
     kb = mm.dyadic_codes(n, n, 2507)

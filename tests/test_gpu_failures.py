@@ -37,7 +37,7 @@ def test_device_waits_give_up_and_the_context_survives():
 def test_block_product_waits_give_up_and_the_context_survives():
     """The tensor-core kernel of the Cannon ring: a launch whose producer
     issues no loads runs its MMA and epilogue waits out (50 ms), latches
-    the timeout, frees its tensor memory and returns; in both cluster modes
+    the timeout, frees its tensor memory and returns; with either tile shape
     the next run is exact."""
     ensure_built()
     from oracle import cannon as oc
@@ -50,8 +50,8 @@ def test_block_product_waits_give_up_and_the_context_survives():
         cn = gw.gw_cannon_create(seg.ctx, n, p)
         try:
             gw.gw_cannon_set(cn, a_bits, bt_bits)
-            for cluster in (2, 1):
-                gw.gw_cannon_schedule(cn, cluster, 16, 64)
+            for tile_m in (256, 128):
+                gw.gw_cannon_schedule(cn, tile_m, 8)
                 t0 = time.perf_counter()
                 st, expired = gw.gw_cannon_selftest_timeout(cn, 50000)
                 el = time.perf_counter() - t0
