@@ -113,7 +113,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}",
                  f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "50"],
+                 "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
@@ -202,87 +202,93 @@ def replica_rate(pg, world: int, units_per_rank: float, ms: float):
 
 # ------------------------------------------------------------------ oracle
 
-def cpu_oracle_rate(shot, target_s: float, nthreads: int) -> tuple[float, str]:
-    """Oracle Gpts/s on a slab of the workload, sized to ~target_s."""
+def _oracle_slab(shot, nthreads: int, target_s: float):
+    """A z-slab of the workload around the source sized so that one oracle
+    step over it takes about target_s (calibrated on 8 planes)."""
     import oracle
     oracle.build()
     n = N_GRID
     dt = oracle.time_step(shot.h, float(shot.vel.max()))
-    # calibrate on 8 planes
     z0 = max(0, shot.src[2] - 4)
-    probe = shot.vel[z0:z0 + 8]
+    probe = np.ascontiguousarray(shot.vel[z0:z0 + 8])
+    oracle.run(probe, shot.h, 1, dt=dt, nthreads=nthreads)       # page in
     t = time.perf_counter()
-    oracle.run(probe, shot.h, 1, dt=dt, nthreads=nthreads)
-    per_pt = (time.perf_counter() - t) / probe.size
-    nz = int(max(8, min(n, target_s / 2 / (per_pt * n * n))))
+    oracle.run(probe, shot.h, 3, dt=dt, nthreads=nthreads)
+    per_pt_step = (time.perf_counter() - t) / 3 / probe.size
+    nz = int(max(8, min(n, target_s / (per_pt_step * n * n))))
     z0 = max(0, min(n - nz, shot.src[2] - nz // 2))
     slab = np.ascontiguousarray(shot.vel[z0:z0 + nz])
     src = (shot.src[0], shot.src[1], shot.src[2] - z0)
-    # size the timed run to ~target_s from the difference of a 1-step and
-    # a 3-step run (a run has a set-up cost several steps long)
-    def timed(k):
-        t = time.perf_counter()
-        oracle.run(slab, shot.h, k, dt=dt, src=src, f_peak=shot.f_peak,
-                   sponge=shot.sponge, nthreads=nthreads)
-        return time.perf_counter() - t
-    per_step = max((timed(3) - timed(1)) / 2, 1e-4)
-    steps = int(max(2, min(2000, round(target_s / per_step))))
+    return slab, src, dt, per_pt_step
+
+
+def cpu_oracle_rate(shot, target_s: float, nthreads: int) -> tuple[float, str]:
+    """Oracle Gpts/s on a slab of the workload: one run of several steps
+    (set-up included once), sized to ~target_s."""
+    import oracle
+    slab, src, dt, per = _oracle_slab(shot, nthreads, target_s / 8)
+    steps = int(max(2, min(2000, round(target_s / (per * slab.size)))))
     t = time.perf_counter()
     oracle.run(slab, shot.h, steps, dt=dt, src=src, f_peak=shot.f_peak,
                sponge=shot.sponge, nthreads=nthreads)
     el = time.perf_counter() - t
-    rate = slab.size * steps / el / 1e9
-    return rate, f"{n}x{n}x{nz} slab of the 512^3 layered model, {steps} steps, {el:.1f} s"
+    n = N_GRID
+    return (slab.size * steps / el / 1e9,
+            f"{n}x{n}x{slab.shape[0]} slab of the 512^3 layered model, one oracle run "
+            f"of {steps} steps, {el:.1f} s, {nthreads} thread(s)")
+
+
+def bench_config(shot) -> dict:
+    """The workload both arms report (launch details of our kernel are in
+    the line's `launch` object, not here)."""
+    n = N_GRID
+    return {"workload": "layered_512cubed", "grid": [n, n, n],
+            "model": "8 layers, velocities U[1500, 4500] m/s, seed 2506",
+            "sponge": shot.sponge, "source_hz": shot.f_peak,
+            "receivers": int(shot.receivers.shape[0]),
+            "l2": "inputs larger than L2: 3 fields x 588 MB streamed per step"}
 
 
 def run_reference(args, world, rank, pg):
+    """The FP64 oracle, as it stands, on the host cores.  One call runs the
+    warm-up and the K timed steps (the state stays inside it); a second
+    call runs the warm-up steps alone.  Both pay the same set-up (arrays,
+    coefficients, sponge tables), so K steps over the difference of the two
+    times is the oracle's stepping rate.  The grid is a z-slab of the 512^3
+    workload around the source, the whole grid when K steps of it take
+    under a minute."""
     import workloads
     if rank != 0:
         return 0
-    shot = workloads.layered_cube(N_GRID)
     import oracle
-    oracle.build()
+    shot = workloads.layered_cube(N_GRID)
     cores = os.cpu_count() or 1
-    dt = oracle.time_step(shot.h, float(shot.vel.max()))
-    n = N_GRID
-    # one bounded slab per step: pick its depth so the run takes minutes
-    probe = np.ascontiguousarray(shot.vel[:8])
-    t = time.perf_counter()
-    oracle.run(probe, shot.h, 1, dt=dt, nthreads=cores)
-    per_pt = (time.perf_counter() - t) / probe.size
-    budget = 120.0 / max(1, args.steps + args.warmup)
-    nz = int(max(8, min(n, budget / (per_pt * n * n))))
-    z0 = max(0, min(n - nz, shot.src[2] - nz // 2))
-    slab = np.ascontiguousarray(shot.vel[z0:z0 + nz])
-    src = (shot.src[0], shot.src[1], shot.src[2] - z0)
-    state = None
+    slab, src, dt, _ = _oracle_slab(shot, cores, 60.0 / max(1, args.steps))
 
-    def one(state):
-        u0, um1 = (None, None) if state is None else state
-        r = oracle.run(slab, shot.h, 1, dt=dt, src=src, f_peak=shot.f_peak,
-                       sponge=shot.sponge, u0=u0, um1=um1, nthreads=cores)
-        return r["u"], r["u_prev"]
+    def timed(k):
+        t = time.perf_counter()
+        oracle.run(slab, shot.h, k, dt=dt, src=src, f_peak=shot.f_peak,
+                   sponge=shot.sponge, nthreads=cores)
+        return time.perf_counter() - t
 
-    for _ in range(args.warmup):
-        state = one(state)
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        state = one(state)
-    el = time.perf_counter() - t
+    t_all = timed(args.warmup + args.steps)
+    t_warm = timed(args.warmup)
+    el = max(t_all - t_warm, 1e-9)
     value = slab.size * args.steps / el / 1e9
+    n = N_GRID
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / max(1, args.steps) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "layered_512cubed", "grid": [n, n, n],
-                   "sponge": shot.sponge, "source_hz": shot.f_peak,
-                   "slab_per_step": [n, n, nz]},
+        "config": bench_config(shot),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
                          "kind": "oracle",
-                         "sample": f"{n}x{n}x{nz} slab of the 512^3 layered "
-                                   f"model per step"},
+                         "sample": f"{n}x{n}x{slab.shape[0]} slab of the 512^3 layered "
+                                   f"model: one call of {args.warmup}+{args.steps} steps "
+                                   f"({t_all:.1f} s) minus one of {args.warmup} "
+                                   f"({t_warm:.1f} s)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -300,17 +306,19 @@ def seg_bytes(nx, ny, nz, dtype, px=1, py=1, pz=1):
 
 
 def run_shot_device(seg, shot, steps, warmup, dtype="f32", px=1, py=1, pz=1,
-                    timing=True, stream=None, sampler=None, halo_mode=0):
+                    timing=True, stream=None, sampler=None, halo_mode=0,
+                    timing_steps=None):
     """Device-resident timing; returns (elapsed_ms, kernel_stats, info,
     clocks, norms).  The wall time covers `steps` steps launched as the
-    library does by default (graph-replayed chunks, overlapped halo
-    copies); kernel statistics come from a separate pass of per-launch
-    CUDA events over min(steps, 100) steps."""
+    library does by default (graph-replayed chunks); kernel statistics come
+    from a separate pass of per-launch CUDA events (timing_steps, default
+    min(steps, 100)).  The clock sampler, if any, runs from the warm-up to
+    the end of the timed steps."""
     import torch
     from paper_2506_02486_gb300 import gbwave as gw
     from paper_2506_02486_gb300.runtime import Shot
     n = N_GRID
-    tsteps = min(steps, 100) if timing else 0
+    tsteps = (timing_steps or min(steps, 100)) if timing else 0
     with Shot(seg, n, n, n, px=px, py=py, pz=pz,
               nsteps=steps + warmup + tsteps, dtype=dtype,
               sponge=shot.sponge, halo_mode=halo_mode) as s:
@@ -318,6 +326,9 @@ def run_shot_device(seg, shot, steps, warmup, dtype="f32", px=1, py=1, pz=1,
         s.add_ricker(shot.src, shot.f_peak)
         s.set_receivers(shot.receivers)
         st = stream or torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
         s.step(warmup, st)
         gw.gw_barrier(s.dom, st, True)
         stats = None
@@ -331,8 +342,6 @@ def run_shot_device(seg, shot, steps, warmup, dtype="f32", px=1, py=1, pz=1,
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        if sampler:
-            sampler.start()
         e0.record(st)
         s.step(steps, st)
         e1.record(st)
@@ -458,6 +467,18 @@ def run_batch(dtype="f32", *, seed=BATCH_SEED, steps=BATCH_STEPS,
     return out
 
 
+def _variant_line(npts, vms, vs, vstats, bpp):
+    kavg = vstats["total_ms"] / max(1, vstats["launches"])
+    return {
+        "gpts": npts * vs / (vms * 1e-3) / 1e9,
+        "kernel_ms": kavg,
+        "halo_kernel_ms": vstats["halo_ms"] / max(1, vstats["launches"]),
+        "alg_bytes_per_point": bpp,
+        "roofline_frac": bpp * npts / (kavg * 1e-3) / 1e9 / measured_peak()[0],
+        "steps": vs,
+    }
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
     import workloads
@@ -469,13 +490,15 @@ def run_ours(args, world, rank, local, pg):
     shot = workloads.layered_cube(N_GRID)
     n = N_GRID
     npts = n ** 3
-    seg = Segment(seg_bytes(n, n, n, "f32", 2, 2, 2), nranks=8, device=local)
     seg1 = Segment(seg_bytes(n, n, n, "f32"), nranks=1, device=local)
     try:
         sampler = ClockSampler(local) if rank == 0 else None
         barrier(pg)
+        # per-launch timing over >= 1500 steps (~0.6 s), so that the clock
+        # samples of the window see the kernel under load
         ms, stats, info, clocks, norms = run_shot_device(
-            seg1, shot, args.steps, args.warmup, sampler=sampler)
+            seg1, shot, args.steps, args.warmup, sampler=sampler,
+            timing_steps=max(args.steps, 1500))
         ms_max, rate = replica_rate(pg, world, npts * args.steps, ms)
         value = rate / 1e9
         # e2e through the public API with host buffers
@@ -486,55 +509,62 @@ def run_ours(args, world, rank, local, pg):
         variants = {}
         if args.variants:
             vs = max(100, args.steps // 5)
-            for name, kw in (("f32_2x2x2_fused_halo", dict(px=2, py=2, pz=2)),
-                             ("f32_2x2x2_separate_halo",
-                              dict(px=2, py=2, pz=2, halo_mode=1)),
-                             ("f16s_delta", dict(dtype="f16s")),
+            for name, kw in (("f16s_delta", dict(dtype="f16s")),
                              ("bf16_delta", dict(dtype="bf16"))):
-                segv = seg if name.startswith("f32_2x2x2") else seg1
-                vms, vstats, _, _, _ = run_shot_device(
-                    segv, shot, vs, args.warmup, **kw)
-                kavg = vstats["total_ms"] / max(1, vstats["launches"])
-                bpp = 10 if kw.get("dtype") in ("f16s", "bf16") else 16
-                variants[name] = {
-                    "gpts": npts * vs / (vms * 1e-3) / 1e9,
-                    "kernel_ms": kavg,
-                    "halo_kernel_ms": vstats["halo_ms"] / max(1, vstats["launches"]),
-                    "alg_bytes_per_point": bpp,
-                    "roofline_frac": bpp * npts / (kavg * 1e-3) / 1e9 / measured_peak()[0],
-                    "steps": vs,
-                }
-            variants[f"cannon_{CANNON_N}_p{CANNON_P}"] = run_cannon(device=local)
-            variants[f"f32_{MINIMOD_N}cubed"] = run_minimod_size(device=local)
-            for dt in ("f32", "bf16"):
-                for suffix, kw in (("", {}), ("_persistent", dict(persistent=True))):
-                    r = run_batch(dt, **kw)
-                    variants[f"batch64_{dt}{suffix}"] = {
-                        k: r[k] for k in ("gpts", "ms", "steps", "chunk",
-                                          "points", "groups", "ctas", "seed",
-                                          "autotune_s", "persistent")}
+                vms, vstats, _, _, _ = run_shot_device(seg1, shot, vs, args.warmup, **kw)
+                variants[name] = _variant_line(npts, vms, vs, vstats, 10)
     finally:
-        seg.close()
         seg1.close()
+    if args.variants:
+        # decompositions inside one HBM: 2 x 2 x 2 cubes and the paper's
+        # 1-D x slabs (Listing 1), halos put by the step kernel or copied by
+        # a separate kernel after it
+        for dec in ((2, 2, 2), (8, 1, 1)):
+            tag = "x".join(map(str, dec))
+            with Segment(seg_bytes(n, n, n, "f32", *dec), nranks=8, device=local) as seg:
+                for mode, hm in (("fused_halo", 0), ("separate_halo", 1)):
+                    vms, vstats, _, _, _ = run_shot_device(
+                        seg, shot, vs, args.warmup, px=dec[0], py=dec[1], pz=dec[2],
+                        halo_mode=hm)
+                    variants[f"f32_{tag}_{mode}"] = _variant_line(npts, vms, vs, vstats, 16)
+        variants[f"cannon_{CANNON_N}_p{CANNON_P}"] = run_cannon(device=local)
+        variants[f"f32_{MINIMOD_N}cubed"] = run_minimod_size(device=local)
+        for dt in ("f32", "bf16"):
+            for suffix, kw in (("", {}), ("_persistent", dict(persistent=True))):
+                r = run_batch(dt, **kw)
+                variants[f"batch64_{dt}{suffix}"] = {
+                    k: r[k] for k in ("gpts", "ms", "steps", "chunk",
+                                      "points", "groups", "ctas", "seed",
+                                      "autotune_s", "persistent")}
+    precision = None
+    if args.variants and args.precision_check:
+        precision = precision_results(500, device=local)
     serving = None
     if args.serving and args.variants:
-        # the first 200 requests of the serving stream, replayed at the same
-        # offered load: p50/p99 latency beside the throughput numbers
-        srv = run_serve(200, device=local)
+        # the first 200 requests of the serving stream at 0.7 of the 64-shot
+        # FP32 batch throughput measured above: p50/p99 latency beside the
+        # throughput numbers
+        srv = run_serve(200, device=local,
+                        capacity_gpts=variants["batch64_f32"]["gpts"])
         serving = {k: srv[k] for k in (
-            "requests", "rate_per_s", "offered_load", "failed",
-            "p50_latency_s", "p99_latency_s", "aggregate_gpts", "busy_gpts",
-            "makespan_s", "max_active", "budget_bytes")}
+            "requests", "rate_per_s", "offered_load", "capacity_gpts_assumed",
+            "failed", "p50_latency_s", "p99_latency_s", "aggregate_gpts",
+            "busy_gpts", "makespan_s", "max_active", "budget_bytes")}
     if rank != 0:
         return 0
     peak, peak_kind = measured_peak()
     kavg_ms = stats["total_ms"] / max(1, stats["launches"])
     achieved = ALG_BYTES_PER_POINT * npts / (kavg_ms * 1e-3) / 1e9
     traffic = recorded_traffic()
-    cpu_rate, cpu_sample = (None, None)
+    cpu = None
     cores = os.cpu_count() or 1
     if args.cpu_baseline:
-        cpu_rate, cpu_sample = cpu_oracle_rate(shot, 20.0, cores)
+        rate, sample = cpu_oracle_rate(shot, 20.0, cores)
+        rate1, sample1 = cpu_oracle_rate(shot, 8.0, 1)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": sample,
+               "one_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                              "sample": sample1}}
     # the timed region: one step kernel per step, one norm reduction per
     # 25-step chunk
     gpu_launches = args.steps + -(-args.steps // 25)
@@ -544,15 +574,14 @@ def run_ours(args, world, rank, local, pg):
         "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {
-            "workload": "layered_512cubed", "grid": [n, n, n],
-            "sponge": shot.sponge, "source_hz": shot.f_peak,
-            "receivers": int(shot.receivers.shape[0]),
+        "config": bench_config(shot),
+        "launch": {
             "decomposition": "1x1x1", "halo": "fused",
             "parallelism": f"replicas{world}",
             "tile": info["tile"], "ctas": info["ctas"], "items": info["items"],
-            "l2": "inputs larger than L2: 3 fields x 588 MB streamed per step",
-            "timing": "CUDA events on the launching stream, per-launch events",
+            "timing": "CUDA events on the launching stream; roofline from "
+                      "per-launch events over a separate pass of "
+                      f"{max(args.steps, 1500)} steps",
         },
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -571,35 +600,37 @@ def run_ours(args, world, rank, local, pg):
         "gpu_launches": gpu_launches,
         "clocks": clocks,
         "variants": variants,
+        "precision": precision,
         "serving": serving,
         "kernel_hash": kernel_hash(),
     }
-    if cpu_rate is not None:
-        line["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT,
-                                "cores": cores, "kind": "oracle",
-                                "sample": cpu_sample}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
     return 0
 
 
 SERVE_SEED = 2509
 SERVE_BUDGET = 150 << 30
-SERVE_CAPACITY_GPTS = 245.0   # measured 64-shot FP32 batch throughput
 SERVE_LOAD = 0.7
 
 
 def run_serve(n=2000, *, seed=SERVE_SEED, load=SERVE_LOAD, slots=64,
-              budget=SERVE_BUDGET, chunk=BATCH_CHUNK, device=0):
+              budget=SERVE_BUDGET, chunk=BATCH_CHUNK, device=0,
+              capacity_gpts=None):
     """Replay a Poisson stream of shot requests in real time through the
     continuous-batching server; latency is arrival -> traces on the host.
     The arrival rate is set so that the offered work is `load` times the
-    measured batched FP32 capacity."""
+    batched FP32 capacity (capacity_gpts: measured in the same run, else
+    measured here first)."""
     import torch
     import workloads
     from paper_2506_02486_gb300.runtime import Segment, Server
+    if capacity_gpts is None:
+        capacity_gpts = run_batch("f32")["gpts"]
     reqs = workloads.arrival_stream(seed, n=n, rate_per_s=1.0)
     work = [r.nx * r.ny * r.nz * r.nsteps for r in reqs]
-    lam = load * SERVE_CAPACITY_GPTS * 1e9 / (sum(work) / len(work))
+    lam = load * capacity_gpts * 1e9 / (sum(work) / len(work))
     # same draws, rescaled inter-arrival times
     arrivals = [r.arrival_s / lam for r in reqs]
     torch.cuda.empty_cache()          # earlier segments' blocks
@@ -637,7 +668,7 @@ def run_serve(n=2000, *, seed=SERVE_SEED, load=SERVE_LOAD, slots=64,
         by_dtype.setdefault(q.dtype, []).append(r["done_s"] - r["submit_s"])
     return {
         "requests": n, "seed": seed, "rate_per_s": lam, "offered_load": load,
-        "capacity_gpts_assumed": SERVE_CAPACITY_GPTS,
+        "capacity_gpts_assumed": capacity_gpts,
         "budget_bytes": budget, "slots": slots, "chunk": chunk,
         "failed": len(bad),
         "p50_latency_s": float(np.percentile(lat, 50)),
@@ -662,7 +693,8 @@ MINIMOD_N = 1200                  # the paper's Minimod grid (section 4.5)
 def run_minimod_size(steps=100, warmup=5, seed=2506, device=0):
     """FP32 Gpts/s on the paper's own Minimod grid, 1200^3 (8-layer model
     set per plane, 20-cell sponge, 20 Hz source, 64 receivers): fields
-    3 x 7 GB, device-resident, per-launch CUDA events."""
+    3 x 7 GB, device-resident, per-launch CUDA events, kernel tile chosen
+    by the library's autotuner for this shape."""
     import torch
     import workloads
     from paper_2506_02486_gb300 import gbwave as gw
@@ -672,7 +704,12 @@ def run_minimod_size(steps=100, warmup=5, seed=2506, device=0):
     src = workloads.source_position(seed + 1, n, n, n, margin=20)
     rec = workloads.lattice_receivers(n, n, 20, n=8, margin=20)
     with Segment(seg_bytes(n, n, n, "f32"), device=device) as seg:
-        with Shot(seg, n, n, n, nsteps=steps + warmup, sponge=20) as s:
+        t0 = time.perf_counter()
+        tile, _, times = gw.gw_autotune(
+            seg.ctx, gw.shot_desc(n, n, n, nsteps=16, sponge=20), steps=6,
+            all_times=True)
+        tune_s = time.perf_counter() - t0
+        with Shot(seg, n, n, n, nsteps=steps + warmup, sponge=20, tile=tile) as s:
             gw.gw_set_model_layered(s.dom, vz)
             s.add_ricker(src, 20.0)
             s.set_receivers(rec)
@@ -692,7 +729,8 @@ def run_minimod_size(steps=100, warmup=5, seed=2506, device=0):
             "kernel_ms": kms, "alg_bytes_per_point": ALG_BYTES_PER_POINT,
             "roofline_frac": ALG_BYTES_PER_POINT * npts / (kms * 1e-3) / 1e9 /
                              measured_peak()[0],
-            "tile": info["tile"], "items": info["items"]}
+            "tile": info["tile"], "items": info["items"],
+            "autotune_ms_per_tile": times, "autotune_s": tune_s}
 
 
 def run_cannon(n=CANNON_N, p=CANNON_P, runs=3, tile_m=256, group=4,
@@ -771,16 +809,20 @@ def run_batch_modes(args):
 
 def run_case(args):
     """One plain shot of an N^3 layered model (no timing extras): the
-    workload the ncu captures profile."""
+    workload the ncu captures profile.  --split PX,PY,PZ decomposes it into
+    subdomains with halos put by the step kernel (--halo fused) or copied by
+    the separate kernel (--halo separate)."""
     import workloads
     from paper_2506_02486_gb300 import buildlib
-    from paper_2506_02486_gb300.runtime import Segment, Shot, padded_bytes
+    from paper_2506_02486_gb300.runtime import Segment, Shot
     buildlib.build()
     n = args.case
+    px, py, pz = (int(v) for v in args.split.split(","))
     shot = workloads.layered_cube(n)
-    with Segment(4 * padded_bytes(n, n, n, args.dtype) + (512 << 20)) as seg:
-        with Shot(seg, n, n, n, nsteps=args.steps, sponge=shot.sponge,
-                  dtype=args.dtype, chunk=-1, tile=args.tile) as s:
+    with Segment(seg_bytes(n, n, n, args.dtype, px, py, pz), nranks=px * py * pz) as seg:
+        with Shot(seg, n, n, n, px=px, py=py, pz=pz, nsteps=args.steps,
+                  sponge=shot.sponge, dtype=args.dtype, chunk=-1, tile=args.tile,
+                  halo_mode=0 if args.halo == "fused" else 1) as s:
             s.set_model(shot.vel)
             s.add_ricker(shot.src, shot.f_peak)
             s.set_receivers(shot.receivers)
@@ -788,36 +830,36 @@ def run_case(args):
             s.sync()
             info = s.info
     print(json.dumps({"case": n, "dtype": args.dtype, "steps": args.steps,
+                      "split": [px, py, pz], "halo": args.halo,
                       "tile": info["tile"], "ctas": info["ctas"],
                       "items": info["items"]}), flush=True)
     return 0
 
 
-def run_precision(args):
-    """Storage types on the 1024 x 1024 x 512 perturbed layered model, 500
-    steps: Gpts/s of each and its error against the FP64 GPU path (whose
-    agreement with the oracle is pinned on a 128^3 crop by the tests)."""
+def precision_results(steps=500, device=0):
+    """Storage types on the 1024 x 1024 x 512 perturbed layered model:
+    Gpts/s of each and its error against the FP64 GPU path (whose agreement
+    with the oracle is pinned on a 128^3 crop by the tests), the same run of
+    `steps` steps for every type."""
     import torch
     import workloads
-    from paper_2506_02486_gb300 import buildlib
     from paper_2506_02486_gb300 import gbwave as gw
     from paper_2506_02486_gb300.runtime import Segment, Shot, padded_bytes
-    buildlib.build()
     shot = workloads.perturbed_box()
     nz, ny, nx = shot.vel.shape
     # receivers on the source plane: within reach of the wave after 500
     # steps (the z = 20 lattice is ~250 cells away and records nothing)
     rec = workloads.lattice_receivers(nx, ny, int(shot.src[2]), n=16,
                                       margin=shot.sponge)
-    steps = args.steps if args.steps != 1000 else shot.nsteps
     npts = nx * ny * nz
+    vel32 = np.ascontiguousarray(shot.vel, dtype=np.float32)
     res, ref = {}, None
     for dt in ("f64", "f32", "f16s", "bf16"):
         nf = 4 if dt in ("f16s", "bf16") else 3
-        with Segment(nf * padded_bytes(nx, ny, nz, dt) + (1 << 30)) as seg:
+        with Segment(nf * padded_bytes(nx, ny, nz, dt) + (1 << 30), device=device) as seg:
             with Shot(seg, nx, ny, nz, nsteps=steps, dtype=dt,
                       sponge=shot.sponge) as s:
-                gw.gw_set_model_f32(s.dom, shot.vel)
+                gw.gw_set_model_f32(s.dom, vel32)
                 s.add_ricker(shot.src, shot.f_peak)
                 s.set_receivers(rec)
                 s.sync()
@@ -846,8 +888,16 @@ def run_precision(args):
     res["max_abs_u"] = float(np.abs(ref[0]).max())
     for dt in ("f16s", "bf16"):
         res[dt]["speedup_vs_f32"] = res[dt]["gpts"] / res["f32"]["gpts"]
-    print(json.dumps({"precision": shot.name, "steps": steps,
-                      "sponge": shot.sponge, "results": res}), flush=True)
+    return {"workload": shot.name, "grid": [nx, ny, nz], "steps": steps,
+            "sponge": shot.sponge, "reference": "FP64 GPU path",
+            "results": res}
+
+
+def run_precision(args):
+    from paper_2506_02486_gb300 import buildlib
+    buildlib.build()
+    steps = args.steps if args.steps != 1000 else 500
+    print(json.dumps({"precision": precision_results(steps)}), flush=True)
     return 0
 
 
@@ -862,10 +912,15 @@ def main():
                     help="skip the 200-request serving replay of the default run")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline",
                     action="store_false")
+    ap.add_argument("--no-precision", dest="precision_check", action="store_false",
+                    help="skip the storage-type errors of the default run")
     ap.add_argument("--case", type=int, default=0,
                     help="run one plain N^3 shot for --steps steps (profiling)")
     ap.add_argument("--dtype", default="f32", help="storage type for --case")
     ap.add_argument("--tile", type=int, default=0, help="kernel tile for --case")
+    ap.add_argument("--split", default="1,1,1", help="subdomains PX,PY,PZ for --case")
+    ap.add_argument("--halo", choices=["fused", "separate"], default="fused",
+                    help="halo mode of a decomposed --case")
     ap.add_argument("--precision", action="store_true",
                     help="storage types vs FP64 on the 1024x1024x512 model")
     ap.add_argument("--serve", type=int, default=0, metavar="N",

@@ -8,6 +8,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "check_sums.cuh"
 #include "gw_device.h"
 #include "gw_kernels.h"
 
@@ -294,66 +295,23 @@ cudaError_t launch_chunk_end(const ShotDev *shots_dev, int nshots,
 
 // ---------------------------------------------------------------- checks
 
-// One block per interior plane z of a subdomain: (sum u^2, sum (u - up)^2
-// / coef, sum u lap(up)) of the plane to part[3 z .. 3 z + 2], summed in a
-// fixed order (no atomics), so that a check is reproducible bit for bit.
+// One block per interior plane z of a subdomain (check_sums.cuh).
 template <class T, class CT>
-__global__ void k_check(SubDev sd, int cur, int xo, double isu, double *part)
+__global__ void __launch_bounds__(kCheckThreads)
+k_check(SubDev sd, int cur, int xo, double isu, double *part)
 {
-    const double c[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0,
-                         -1.0 / 560.0};
-    const T *un = reinterpret_cast<const T *>(sd.u[cur]);
-    const T *up = reinterpret_cast<const T *>(sd.u[cur ^ 1]);
-    const CT *cf = reinterpret_cast<const CT *>(sd.coef);
     const int z = blockIdx.x;
-    const int npl = sd.nx * sd.ny;
-    double a0 = 0, a1 = 0, a2 = 0;
-    const long long sx = 1, sy = sd.px, sz = (long long)sd.px * sd.py;
-    for (int i = threadIdx.x; i < npl; i += blockDim.x) {
-        int x = i % sd.nx;
-        int y = i / sd.nx;
-        size_t p = pidx(sd, xo, x, y, z);
-        double u = to_d<T>(un[p]) * isu;
-        double v = to_d<T>(up[p]) * isu;
-        double lap = 3.0 * c[0] * v;
-        for (int m = 1; m <= 4; ++m)
-            lap += c[m] * (to_d<T>(up[p - m * sx]) + to_d<T>(up[p + m * sx]) +
-                           to_d<T>(up[p - m * sy]) + to_d<T>(up[p + m * sy]) +
-                           to_d<T>(up[p - m * sz]) + to_d<T>(up[p + m * sz])) * isu;
-        double d = u - v;
-        a0 += u * u;
-        a1 += d * d / to_d<CT>(cf[p]);
-        a2 += u * lap;
-    }
-    __shared__ double red[3][256];
-    red[0][threadIdx.x] = a0;
-    red[1][threadIdx.x] = a1;
-    red[2][threadIdx.x] = a2;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o)
-            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) part[3 * z + k] = red[k][0];
+    check_plane_sums<T, CT>(reinterpret_cast<const T *>(sd.u[cur]),
+                            reinterpret_cast<const T *>(sd.u[cur ^ 1]),
+                            reinterpret_cast<const CT *>(sd.coef), sd.nx, sd.ny,
+                            (long long)pidx(sd, xo, 0, 0, z), sd.px,
+                            (long long)sd.px * sd.py, isu, part + 3 * z);
 }
 
-__global__ void k_check_sum(const double *part, int nplanes, double *out)
+__global__ void __launch_bounds__(kCheckThreads)
+k_check_sum(const double *part, int nplanes, double *out)
 {
-    __shared__ double red[3][256];
-    double a[3] = {0, 0, 0};
-    for (int z = threadIdx.x; z < nplanes; z += blockDim.x)
-        for (int k = 0; k < 3; ++k) a[k] += part[3 * z + k];
-    for (int k = 0; k < 3; ++k) red[k][threadIdx.x] = a[k];
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o)
-            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) out[k] = red[k][0];
+    check_sum_planes(part, nplanes, out);
 }
 
 cudaError_t launch_check(const SubDev &sd, int cur, int dtype, double scale_u,
@@ -363,10 +321,12 @@ cudaError_t launch_check(const SubDev &sd, int cur, int dtype, double scale_u,
     const int xo = dtype_xoff(dtype);
     const double isu = 1.0 / scale_u;
     switch (dtype) {
-    case DT_F32: k_check<float, float><<<g, 256, 0, s>>>(sd, cur, xo, isu, part); break;
-    case DT_F64: k_check<double, double><<<g, 256, 0, s>>>(sd, cur, xo, isu, part); break;
-    case DT_F16S: k_check<__half, __half><<<g, 256, 0, s>>>(sd, cur, xo, isu, part); break;
-    case DT_BF16: k_check<__nv_bfloat16, __half><<<g, 256, 0, s>>>(sd, cur, xo, isu, part); break;
+    case DT_F32: k_check<float, float><<<g, kCheckThreads, 0, s>>>(sd, cur, xo, isu, part); break;
+    case DT_F64: k_check<double, double><<<g, kCheckThreads, 0, s>>>(sd, cur, xo, isu, part); break;
+    case DT_F16S: k_check<__half, __half><<<g, kCheckThreads, 0, s>>>(sd, cur, xo, isu, part); break;
+    case DT_BF16:
+        k_check<__nv_bfloat16, __half><<<g, kCheckThreads, 0, s>>>(sd, cur, xo, isu, part);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -374,7 +334,7 @@ cudaError_t launch_check(const SubDev &sd, int cur, int dtype, double scale_u,
 
 cudaError_t launch_check_sum(const double *part, int nplanes, double *out, cudaStream_t s)
 {
-    k_check_sum<<<1, 256, 0, s>>>(part, nplanes, out);
+    k_check_sum<<<1, kCheckThreads, 0, s>>>(part, nplanes, out);
     return cudaGetLastError();
 }
 

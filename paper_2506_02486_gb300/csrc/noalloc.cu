@@ -15,6 +15,7 @@
 
 #include <mutex>
 
+#include "check_sums.cuh"
 #include "gw_internal.h"
 
 namespace gw {
@@ -26,69 +27,23 @@ static __device__ __align__(256) double g_noalloc_partials[kNoallocMaxPlanes * 3
 
 namespace {
 
-template <class T> __device__ __forceinline__ double ld_d(const T *p);
-template <> __device__ __forceinline__ double ld_d<float>(const float *p) { return *p; }
-template <> __device__ __forceinline__ double ld_d<double>(const double *p) { return *p; }
-template <> __device__ __forceinline__ double ld_d<__half>(const __half *p) { return (double)__half2float(*p); }
-template <> __device__ __forceinline__ double ld_d<__nv_bfloat16>(const __nv_bfloat16 *p) { return (double)__bfloat162float(*p); }
-
-// One block per interior plane z: writes (sum u^2, sum (u - up)^2 / coef,
-// sum u lap(up)) of that plane to part[3 z .. 3 z + 2].
+// One block per interior plane z of a caller's padded fields: the same
+// sums, in the same order, as gw_check (check_sums.cuh).
 template <class T, class CT>
-__global__ void k_plane_sums(const T *un, const T *up, const CT *cf, int nx,
-                             int ny, int px, int xo, double isu, double *part)
+__global__ void __launch_bounds__(kCheckThreads)
+k_plane_sums(const T *un, const T *up, const CT *cf, int nx, int ny, int px, int xo,
+             double isu, double *part)
 {
     const int z = blockIdx.x;
-    const double c[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0,
-                         -1.0 / 560.0};
-    const long long py = ny + 2 * R;
-    const long long sy = px, sz = (long long)px * py;
-    double a0 = 0, a1 = 0, a2 = 0;
-    for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) {
-        const int x = i % nx, y = i / nx;
-        const long long p = (long long)(z + R) * sz + (long long)(y + R) * sy + xo + x;
-        const double u = ld_d(un + p) * isu;
-        const double v = ld_d(up + p) * isu;
-        double lap = 3.0 * c[0] * v;
-        for (int m = 1; m <= 4; ++m)
-            lap += c[m] * (ld_d(up + p - m) + ld_d(up + p + m) + ld_d(up + p - m * sy) +
-                           ld_d(up + p + m * sy) + ld_d(up + p - m * sz) +
-                           ld_d(up + p + m * sz)) * isu;
-        const double d = u - v;
-        a0 += u * u;
-        a1 += d * d / ld_d(cf + p);
-        a2 += u * lap;
-    }
-    __shared__ double red[3][256];
-    red[0][threadIdx.x] = a0;
-    red[1][threadIdx.x] = a1;
-    red[2][threadIdx.x] = a2;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o)
-            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) part[3 * z + k] = red[k][0];
+    const long long sy = px, sz = (long long)px * (ny + 2 * R);
+    check_plane_sums<T, CT>(un, up, cf, nx, ny, (long long)(z + R) * sz + R * sy + xo, sy, sz,
+                            isu, part + 3 * z);
 }
 
-// Sums the plane partials in a fixed order into out[0..2].
-__global__ void k_sum_planes(const double *part, int nz, double *out)
+__global__ void __launch_bounds__(kCheckThreads)
+k_sum_planes(const double *part, int nz, double *out)
 {
-    __shared__ double red[3][256];
-    double a[3] = {0, 0, 0};
-    for (int z = threadIdx.x; z < nz; z += blockDim.x)
-        for (int k = 0; k < 3; ++k) a[k] += part[3 * z + k];
-    for (int k = 0; k < 3; ++k) red[k][threadIdx.x] = a[k];
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o)
-            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) out[k] = red[k][0];
+    check_sum_planes(part, nz, out);
 }
 
 // Device address of the scratch array, looked up once per device with that
@@ -139,29 +94,29 @@ extern "C" gw_status gw_check_fields_noalloc(const void *u_cur, const void *u_pr
     const double isu = 1.0 / scale_u;
     switch (dtype) {
     case DT_F32:
-        k_plane_sums<float, float><<<nz, 256, 0, s>>>(
+        k_plane_sums<float, float><<<nz, kCheckThreads, 0, s>>>(
             static_cast<const float *>(u_cur), static_cast<const float *>(u_prev),
             static_cast<const float *>(coef), nx, ny, px, xo, isu, part);
         break;
     case DT_F64:
-        k_plane_sums<double, double><<<nz, 256, 0, s>>>(
+        k_plane_sums<double, double><<<nz, kCheckThreads, 0, s>>>(
             static_cast<const double *>(u_cur), static_cast<const double *>(u_prev),
             static_cast<const double *>(coef), nx, ny, px, xo, isu, part);
         break;
     case DT_F16S:
-        k_plane_sums<__half, __half><<<nz, 256, 0, s>>>(
+        k_plane_sums<__half, __half><<<nz, kCheckThreads, 0, s>>>(
             static_cast<const __half *>(u_cur), static_cast<const __half *>(u_prev),
             static_cast<const __half *>(coef), nx, ny, px, xo, isu, part);
         break;
     default:
-        k_plane_sums<__nv_bfloat16, __half><<<nz, 256, 0, s>>>(
+        k_plane_sums<__nv_bfloat16, __half><<<nz, kCheckThreads, 0, s>>>(
             static_cast<const __nv_bfloat16 *>(u_cur),
             static_cast<const __nv_bfloat16 *>(u_prev),
             static_cast<const __half *>(coef), nx, ny, px, xo, isu, part);
         break;
     }
     GW_TRY_CUDA(cudaGetLastError());
-    k_sum_planes<<<1, 256, 0, s>>>(part, nz, out_dev);
+    k_sum_planes<<<1, kCheckThreads, 0, s>>>(part, nz, out_dev);
     GW_TRY_CUDA(cudaGetLastError());
     return GW_OK;
 }

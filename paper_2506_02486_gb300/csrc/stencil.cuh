@@ -339,8 +339,14 @@ struct Step {
     static constexpr int KP = C::KP;
     static_assert(KP == 2 || KP == 4, "planes per trip");
     G gxy[PY];                 // g_x g_y of this thread's points
-    M acc;
-    float2 acc2;               // packed FP32 norm partials
+    // sum of u'^2: a thread's (at most 4 PY = 8) points of one plane are
+    // summed in the math type; the plane sums are accumulated as an
+    // unevaluated pair (nacc + ncomp) by error-free transformations (TwoSum,
+    // the cascaded summation "Sum2" of Ogita, Rump and Oishi, 2005), which
+    // is as accurate as an FP64 accumulator, and the pair is added in FP64
+    // at the end of the item.  (An FP64 add per plane stalls every warp on
+    // GB300's narrow FP64 pipe: -1 % FP32, -9 % 16-bit storage at 512^3.)
+    M nacc, ncomp;
     G Q[8 + KP][PY];           // this thread's points on planes z-4 .. z+4+KP-1
 
     __device__ Step(const StepArgs &a, unsigned char *sm) : A(a), smem(sm) {}
@@ -499,8 +505,8 @@ struct Step {
                 }
             }
         }
-        acc = M(0);
-        acc2 = make_float2(0.0f, 0.0f);
+        nacc = M(0);
+        ncomp = M(0);
         // receivers and sources inside this item -> shared list (warp 0)
         if (tid < 32) {
             int cnt = 0;
@@ -576,7 +582,7 @@ struct Step {
 
     __device__ __forceinline__ void end_item(int it)
     {
-        double v = (double)acc + (double)acc2.x + (double)acc2.y;
+        double v = (double)nacc + (double)ncomp;
         if (SCALED) v *= (double)isu_ * (double)isu_;   // sums of (su u)^2
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -713,19 +719,33 @@ struct Step {
         }
     }
 
-    // sum of u'^2 over this thread's valid points (per-lane FP32 partials)
-    __device__ __forceinline__ void accumulate_norm(const G &un)
+    // sum of u'^2 over this thread's valid points of one row into the
+    // plane's partials (pp: packed lanes, ps: scalar)
+    __device__ __forceinline__ void accumulate_norm(const G &un, float2 &pp, M &ps)
     {
         if constexpr (PK) {
             if (vx == 4) {
-                acc2 = __ffma2_rn(un.a, un.a, acc2);
-                acc2 = __ffma2_rn(un.b, un.b, acc2);
+                pp = __ffma2_rn(un.a, un.a, pp);
+                pp = __ffma2_rn(un.b, un.b, pp);
                 return;
             }
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            if (i < vx) acc = fma_rn(un.get(i), un.get(i), acc);
+            if (i < vx) ps = fma_rn(un.get(i), un.get(i), ps);
+    }
+
+    // the plane's partial sum of squares x into the pair (nacc, ncomp):
+    // TwoSum gives nacc + x = t + e exactly, e is added to the compensation
+    __device__ __forceinline__ void add_plane_norm(const float2 &pp, M ps)
+    {
+        M x = ps;
+        if constexpr (PK) x = add_rn(add_rn(pp.x, pp.y), ps);
+        const M t = add_rn(nacc, x);
+        const M bp = add_rn(t, -nacc);
+        const M e = add_rn(add_rn(nacc, -add_rn(t, -bp)), add_rn(x, -bp));
+        nacc = t;
+        ncomp = add_rn(ncomp, e);
     }
 
     // ---- the z loop of one item --------------------------------------
@@ -810,6 +830,8 @@ struct Step {
             update_row(yv[r + R], pa[r], cf[r], lap[r], gxy[r], gz, un[r], wn[r]);
         // stores: u' (and w') at this plane; norm partial
         const bool zput = PUTS && ((z < R && nbr_[4] >= 0) || (z >= nz - R && nbr_[5] >= 0));
+        float2 nrm2 = make_float2(0.0f, 0.0f);   // this plane's sum of u'^2
+        M nrm = M(0);
 #pragma unroll
         for (int r = 0; r < PY; ++r) {
             T *up = ust + r * (long long)px_;
@@ -821,11 +843,11 @@ struct Step {
             }
             if (FAST) {
                 if constexpr (PK) {
-                    acc2 = __ffma2_rn(un[r].a, un[r].a, acc2);
-                    acc2 = __ffma2_rn(un[r].b, un[r].b, acc2);
+                    nrm2 = __ffma2_rn(un[r].a, un[r].a, nrm2);
+                    nrm2 = __ffma2_rn(un[r].b, un[r].b, nrm2);
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) acc = fma_rn(so[i], so[i], acc);
+                    for (int i = 0; i < 4; ++i) nrm = fma_rn(so[i], so[i], nrm);
                 }
                 S::st4(up, so);
                 if (DELTA) S::st4(up + wdelta, sw);
@@ -833,7 +855,7 @@ struct Step {
                 continue;
             }
             if (!rowok[r] || vx == 0) continue;
-            accumulate_norm(un[r]);
+            accumulate_norm(un[r], nrm2, nrm);
             if (vx == 4) {
                 S::st4(up, so);
                 if (DELTA) S::st4(up + wdelta, sw);
@@ -848,6 +870,7 @@ struct Step {
             }
             if (PUTS && item_puts) put_halo_row(x0 + 4 * tx, y0 + PY * ty + r, z, so);
         }
+        add_plane_norm(nrm2, nrm);
         if (locz) record_receivers(z, un);
         ust += plane_;
         // (4) hand slots back: the compute plane's load (its last use) and

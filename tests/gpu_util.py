@@ -35,6 +35,33 @@ def rel_l2(a, b) -> float:
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def max_rel(a, b) -> float:
+    """Largest point-by-point difference relative to the largest value of
+    the reference: max |a - b| / max |b|.  Unlike the relative L2 norm it
+    does not average a wrong row or a wrong halo cell away over the grid."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def assert_close(g, o, tol, what="u"):
+    """Relative L2 <= tol and max |g - o| <= tol * max |o|."""
+    e2, ei = rel_l2(g, o), max_rel(g, o)
+    assert e2 <= tol, f"{what}: relative L2 {e2:.3e} > {tol:.1e}"
+    assert ei <= tol, f"{what}: max |g - o| / max |o| = {ei:.3e} > {tol:.1e}"
+    return e2, ei
+
+
+# 2^-24: unit roundoff of FP32
+U32 = 2.0 ** -24
+
+
+def gamma(n: int, u: float = U32) -> float:
+    """gamma_n = n u / (1 - n u): the relative error bound of a sum of n + 1
+    positive terms in a precision of unit roundoff u (Higham, eq. 3.8)."""
+    return n * u / (1.0 - n * u)
+
+
 def gpu_run(vel, nsteps, *, h=10.0, src=None, f_peak=None, wavelet=None,
             receivers=None, sponge=0, dtype="f32", px=1, py=1, pz=1,
             split=(None, None, None), symmetric=True, seg=None, u0=None,

@@ -5,14 +5,19 @@ Each shot of a batch must end bit-identical (wavefield and receiver traces)
 to the same shot stepped alone with the same kernel tile: the per-point
 arithmetic does not depend on which launch, CTA or z-chunk computes a
 point.  Per-step norms are FP64 sums over a different set of work items,
-so they agree to rounding (1e-12 relative).
+so they agree to rounding (1e-12 relative).  Every batched shot is also
+checked against the FP64 oracle run of the same shot: FP32 within 1e-4,
+FP64 within 1e-10 (relative L2 and point by point), the 16-bit storage
+types within their stated bounds against FP64 (FP16 with power-of-two
+scales 5e-3, BF16 6e-2).
 """
 
 import numpy as np
 import pytest
 
+import oracle
 import workloads
-from gpu_util import ensure_built
+from gpu_util import assert_close, ensure_built, rel_l2
 from paper_2506_02486_gb300 import gbwave as gw
 from paper_2506_02486_gb300.runtime import Batch, Segment, Shot, shot_bytes
 
@@ -35,14 +40,59 @@ def _make(seg, k, spec, dtype):
              dtype=dtype, sponge=sponge, tile=tile)
     s.set_model(workloads.layered(nx, ny, nz, seed=100 + k))
     s.add_ricker((nx // 2, ny // 3, nz // 2), 30.0)
-    s.set_receivers(workloads.lattice_receivers(nx, ny, nz // 4, n=3,
-                                                margin=2))
+    s.set_receivers(_receivers(spec))
     return s
 
 
+def _receivers(spec):
+    """A cross through the source cell (distances 0, 2, 4 along each axis):
+    within STEPS steps (shorter than the Ricker delay 1 / f) the wave has
+    not travelled further, and ahead of it the values are ~1e-38 noise that
+    16-bit storage rightly flushes to zero."""
+    nx, ny, nz = spec[:3]
+    sx, sy, sz = nx // 2, ny // 3, nz // 2
+    pts = {(sx, sy, sz)}
+    for d in (2, 4):
+        pts |= {(sx + d, sy, sz), (sx, sy + d, sz), (sx, sy, sz + d)}
+    return np.array(sorted(pts), dtype=np.int32)
+
+
 def _result(s):
-    return {"u": s.u(f64=False), "traces": s.traces(STEPS),
+    return {"u": s.u(f64=True), "traces": s.traces(STEPS),
             "norms": s.norms(STEPS)}
+
+
+# bound against the FP64 oracle per storage type
+BOUND = {"f32": 1e-4, "f64": 1e-10, "f16s": 5e-3, "bf16": 6e-2}
+_oracle_cache = {}
+
+
+def _oracle(k):
+    """FP64 oracle run of SHOTS[k] (the inputs _make gives the library)."""
+    if k not in _oracle_cache:
+        nx, ny, nz, px, py, pz, sponge, tile = SHOTS[k]
+        vel = workloads.layered(nx, ny, nz, seed=100 + k)
+        rec = _receivers(SHOTS[k])
+        _oracle_cache[k] = oracle.run(
+            vel, 10.0, STEPS, dt=oracle.time_step(10.0, float(vel.max())),
+            src=(nx // 2, ny // 3, nz // 2), f_peak=30.0, sponge=sponge,
+            receivers=rec, nthreads=8)
+    return _oracle_cache[k]
+
+
+def _against_oracle(k, r, dtype):
+    o = _oracle(k)
+    tol = BOUND[dtype]
+    u = r["u"].astype(np.float64)
+    assert np.abs(o["traces"]).max() > 1e-2 * np.abs(o["u"]).max(), k
+    if dtype in ("f32", "f64"):
+        assert_close(u, o["u"], tol, f"shot {k} u")
+        # traces are recorded in FP32 for every storage type
+        assert_close(r["traces"], o["traces"], max(tol, 2.0 ** -23), f"shot {k} traces")
+    else:
+        # 16-bit storage: the stated bounds are relative L2 bounds
+        assert rel_l2(u, o["u"]) <= tol, (k, rel_l2(u, o["u"]))
+        assert rel_l2(r["traces"], o["traces"]) <= tol, (k, rel_l2(r["traces"], o["traces"]))
 
 
 def _seg_bytes(dtype):
@@ -82,6 +132,7 @@ def test_batched_shots_match_alone(dtype, mode):
                 np.testing.assert_allclose(r["norms"], a["norms"],
                                            rtol=1e-12, atol=0)
                 assert np.abs(a["u"]).max() > 0
+                _against_oracle(k, r, dtype)
         finally:
             for s in shots:
                 s.close()

@@ -16,7 +16,7 @@ import pytest
 
 import oracle
 import workloads
-from gpu_util import gpu_run, rel_l2
+from gpu_util import assert_close, gpu_run
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +41,7 @@ def test_light_cone_box_matches_oracle(shot):
     o = oracle.run(crop, shot.h, n, dt=dt, src=(B, B, B), f_peak=shot.f_peak,
                    nthreads=8)
     gu = g["u"][lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
-    assert rel_l2(gu, o["u"]) <= 1e-4
+    assert_close(gu, o["u"], 1e-4)
     # nothing outside the light cone box
     outside = g["u"].copy()
     outside[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = 0
@@ -89,6 +89,6 @@ def test_light_cone_box_at_the_paper_minimod_grid():
     dt = oracle.time_step(h, float(vz.max()))
     o = oracle.run(crop, h, steps, dt=dt, src=(B, B, B), f_peak=20.0, nthreads=8)
     gu = u[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]].astype(np.float64)
-    assert rel_l2(gu, o["u"]) <= 1e-4
+    assert_close(gu, o["u"], 1e-4)
     u[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = 0
     assert not u.any()
