@@ -307,7 +307,7 @@ def seg_bytes(nx, ny, nz, dtype, px=1, py=1, pz=1):
 
 def run_shot_device(seg, shot, steps, warmup, dtype="f32", px=1, py=1, pz=1,
                     timing=True, stream=None, sampler=None, halo_mode=0,
-                    timing_steps=None):
+                    timing_steps=None, tile=0):
     """Device-resident timing; returns (elapsed_ms, kernel_stats, info,
     clocks, norms).  The wall time covers `steps` steps launched as the
     library does by default (graph-replayed chunks); kernel statistics come
@@ -321,7 +321,7 @@ def run_shot_device(seg, shot, steps, warmup, dtype="f32", px=1, py=1, pz=1,
     tsteps = (timing_steps or min(steps, 100)) if timing else 0
     with Shot(seg, n, n, n, px=px, py=py, pz=pz,
               nsteps=steps + warmup + tsteps, dtype=dtype,
-              sponge=shot.sponge, halo_mode=halo_mode) as s:
+              sponge=shot.sponge, halo_mode=halo_mode, tile=tile) as s:
         s.set_model(shot.vel)
         s.add_ricker(shot.src, shot.f_peak)
         s.set_receivers(shot.receivers)
@@ -519,14 +519,21 @@ def run_ours(args, world, rank, local, pg):
         # decompositions inside one HBM: 2 x 2 x 2 cubes and the paper's
         # 1-D x slabs (Listing 1), halos put by the step kernel or copied by
         # a separate kernel after it
+        from paper_2506_02486_gb300 import gbwave as gw
         for dec in ((2, 2, 2), (8, 1, 1)):
             tag = "x".join(map(str, dec))
             with Segment(seg_bytes(n, n, n, "f32", *dec), nranks=8, device=local) as seg:
                 for mode, hm in (("fused_halo", 0), ("separate_halo", 1)):
-                    vms, vstats, _, _, _ = run_shot_device(
+                    # the kernel tile the library's autotuner picks for the
+                    # subdomain shape
+                    tile, _ = gw.gw_autotune(
+                        seg.ctx, gw.shot_desc(n, n, n, nsteps=16, sponge=shot.sponge,
+                                              halo_mode=hm), *dec, steps=6)
+                    vms, vstats, vinfo, _, _ = run_shot_device(
                         seg, shot, vs, args.warmup, px=dec[0], py=dec[1], pz=dec[2],
-                        halo_mode=hm)
-                    variants[f"f32_{tag}_{mode}"] = _variant_line(npts, vms, vs, vstats, 16)
+                        halo_mode=hm, tile=tile)
+                    variants[f"f32_{tag}_{mode}"] = dict(
+                        _variant_line(npts, vms, vs, vstats, 16), tile=vinfo["tile"])
         variants[f"cannon_{CANNON_N}_p{CANNON_P}"] = run_cannon(device=local)
         variants[f"f32_{MINIMOD_N}cubed"] = run_minimod_size(device=local)
         for dt in ("f32", "bf16"):

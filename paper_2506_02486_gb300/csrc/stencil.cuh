@@ -318,7 +318,6 @@ struct Step {
     bool item_puts;            // fused puts: this tile touches a face with a neighbour
     bool fast_;                // whole tile
     int zloc_lo_, zloc_hi_;    // planes holding this item's sources / receivers
-    bool tput_;                // fused puts: this thread's points touch an x or y face
     T *ust;                    // store address of this thread's first row at the compute plane
     long long wdelta;          // w field minus u_{n+1} field (elements)
     size_t roff_[PY];          // in-plane element offset of each row's first point
@@ -570,12 +569,6 @@ struct Step {
             zloc_lo_ = min(zloc_lo_, zq);
             zloc_hi_ = max(zloc_hi_, zq);
         }
-        {
-            const int xs = x0 + 4 * tx, ys = y0 + PY * ty;
-            tput_ = item_puts &&
-                    ((xs < R && nbr_[0] >= 0) || (xs + 4 > nx - R && nbr_[1] >= 0) ||
-                     (ys < R && nbr_[2] >= 0) || (ys + PY > ny - R && nbr_[3] >= 0));
-        }
         ust = unext + (size_t)(z0 + R) * plane_ + roff_[0];
         wdelta = DELTA ? (long long)(wbuf - unext) : 0;
     }
@@ -771,7 +764,7 @@ struct Step {
 
     // One compute plane z.  FAST: a whole tile (every row and point valid)
     // with no halo puts, sources or receivers.
-    template <int P, bool FAST, bool PUTS, bool LOC>
+    template <int P, bool FAST, bool LOC>
     __device__ __forceinline__ void step_plane(int z)
     {
         // (1) x/y neighbours from the compute plane, staged R loads ago (its
@@ -829,7 +822,6 @@ struct Step {
         for (int r = 0; r < PY; ++r)
             update_row(yv[r + R], pa[r], cf[r], lap[r], gxy[r], gz, un[r], wn[r]);
         // stores: u' (and w') at this plane; norm partial
-        const bool zput = PUTS && ((z < R && nbr_[4] >= 0) || (z >= nz - R && nbr_[5] >= 0));
         float2 nrm2 = make_float2(0.0f, 0.0f);   // this plane's sum of u'^2
         M nrm = M(0);
 #pragma unroll
@@ -851,7 +843,6 @@ struct Step {
                 }
                 S::st4(up, so);
                 if (DELTA) S::st4(up + wdelta, sw);
-                if (PUTS && (tput_ || zput)) put_halo_row(x0 + 4 * tx, y0 + PY * ty + r, z, so);
                 continue;
             }
             if (!rowok[r] || vx == 0) continue;
@@ -868,7 +859,6 @@ struct Step {
                     }
                 }
             }
-            if (PUTS && item_puts) put_halo_row(x0 + 4 * tx, y0 + PY * ty + r, z, so);
         }
         add_plane_norm(nrm2, nrm);
         if (locz) record_receivers(z, un);
@@ -940,64 +930,118 @@ struct Step {
     }
 
     // the compute planes of one item, KP per trip of the loop
-    template <bool FAST, bool PUTS, bool LOC>
+    template <bool FAST, bool LOC>
     __device__ __forceinline__ void z_loop(int nzc)
     {
 #pragma unroll 1
         for (int tb = 0; tb < nzc; tb += KP) {
-            step_plane<0, FAST, PUTS, LOC>(z0 + tb);
-            if (tb + 1 < nzc) step_plane<1, FAST, PUTS, LOC>(z0 + tb + 1);
+            step_plane<0, FAST, LOC>(z0 + tb);
+            if (tb + 1 < nzc) step_plane<1, FAST, LOC>(z0 + tb + 1);
             if constexpr (KP > 2) {
-                if (tb + 2 < nzc) step_plane<2, FAST, PUTS, LOC>(z0 + tb + 2);
-                if (tb + 3 < nzc) step_plane<3, FAST, PUTS, LOC>(z0 + tb + 3);
+                if (tb + 2 < nzc) step_plane<2, FAST, LOC>(z0 + tb + 2);
+                if (tb + 3 < nzc) step_plane<3, FAST, LOC>(z0 + tb + 3);
             }
             shift_queue();
         }
     }
 
-    // One-sided puts of a freshly computed row segment into the halos of
-    // the face neighbours that read it (Listing 1's ompx_put, fused).
-    // mask selects which of the 4 points to store; a full, 16-byte aligned
-    // segment is stored as one vector.
-    __device__ __forceinline__ void put_row(int f, int x, int y, int z,
-                                            const M (&so)[4], unsigned mask)
-    {
-        const NbrPut q = nbrput()[f];
-        T *base = reinterpret_cast<T *>(q.base);
-        const long long off = (long long)(z + R) * q.plane +
-                              (long long)(y + R) * q.px + XO + x;
-        if (mask == 0xFu && ((XO + x) & 3) == 0) {
-            S::st4(base + off, so);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (mask >> i & 1u) S::st1(base + off + i, so[i]);
-        }
-    }
+    // ---- fused halo puts (Listing 1's ompx_put, done by the step kernel) --
+    // After the item's z loop and a consumer barrier (which orders every
+    // consumer thread's stores of the item before the loads below), the
+    // consumer threads copy the item's boundary strips of u_{n+1} -- at most
+    // R cells deep along each face that has a neighbour -- from this
+    // subdomain's field, where they were just stored and still sit in L2,
+    // into the face neighbours' halos.  The z loop of a boundary item is
+    // then the same as an interior item's (per-row put code in the loop
+    // cost 16-45 % in instruction issue and fetch).
 
-    __device__ __forceinline__ void put_halo_row(int x, int y, int z, const M (&so)[4])
-    {
-        const unsigned valid = (1u << vx) - 1u;
-        if (z < R && nbr_[4] >= 0)
-            put_row(4, x, y, nbrput()[4].ext + z, so, valid);
-        if (z >= nz - R && nbr_[5] >= 0)
-            put_row(5, x, y, z - nz, so, valid);
-        if (y < R && nbr_[2] >= 0)
-            put_row(2, x, nbrput()[2].ext + y, z, so, valid);
-        if (y >= ny - R && nbr_[3] >= 0)
-            put_row(3, x, y - ny, z, so, valid);
-        if (x < R && nbr_[0] >= 0) {
-            // points x + i < R go to the -x neighbour's +x halo
-            unsigned m = 0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) m |= (x + i < R ? 1u : 0u) << i;
-            put_row(0, nbrput()[0].ext + x, y, z, so, m & valid);
+    // 4 elements of T moved as one unit: 16 bytes (FP32), 8 (16-bit) or
+    // 2 x 16 (FP64), through L2 only (the source was stored moments ago by
+    // other threads of this CTA; nothing of it is in L1)
+    struct Vec4 {
+        using W = typename std::conditional<sizeof(T) == 2, uint2, uint4>::type;
+        W a, b;
+        __device__ __forceinline__ void load(const T *p)
+        {
+            a = __ldcg(reinterpret_cast<const W *>(p));
+            if constexpr (sizeof(T) == 8) b = __ldcg(reinterpret_cast<const W *>(p) + 1);
         }
-        if (x + vx > nx - R && nbr_[1] >= 0) {
-            unsigned m = 0;
+        __device__ __forceinline__ void store(T *p) const
+        {
+            __stcg(reinterpret_cast<W *>(p), a);
+            if constexpr (sizeof(T) == 8) __stcg(reinterpret_cast<W *>(p) + 1, b);
+        }
+    };
+
+    // What the puts of one item need (passed by value, so that the put code
+    // can live out of line without putting the Step object in memory).
+    struct PutItem {
+        T *u;                  // this subdomain's u_{n+1}
+        const NbrPut *nbr;     // per face: the neighbour's buffer and strides
+        size_t plane;          // this subdomain's plane stride
+        int px;                // and row pitch
+        int x0, y0, z0, z1, nx, ny, nz;
+        int has;               // bit f: face f has a neighbour
+    };
+
+    __device__ __noinline__ static void put_item(const PutItem p, int tid)
+    {
+        constexpr int B = sizeof(T) == 8 ? 4 : 8;   // copies in flight per thread
+        const int xe = min(p.x0 + TX, p.nx), ye = min(p.y0 + TY, p.ny);
+        for (int f = 0; f < 6; ++f) {
+            if (!(p.has >> f & 1)) continue;
+            // the part of this item within R of face f, and where it goes
+            int xl = p.x0, xh = xe, yl = p.y0, yh = ye, zl = p.z0, zh = p.z1;
+            int dx = 0, dy = 0, dz = 0;
+            const NbrPut q = p.nbr[f];
+            switch (f) {
+            case 0: xh = min(xh, R); dx = q.ext; break;        // -> its +x halo
+            case 1: xl = max(xl, p.nx - R); dx = -p.nx; break; // -> its -x halo
+            case 2: yh = min(yh, R); dy = q.ext; break;
+            case 3: yl = max(yl, p.ny - R); dy = -p.ny; break;
+            case 4: zh = min(zh, R); dz = q.ext; break;
+            default: zl = max(zl, p.nz - R); dz = -p.nz; break;
+            }
+            if (xl >= xh || yl >= yh || zl >= zh) continue;
+            const T *src0 = p.u + (size_t)(zl + R) * p.plane + (size_t)(yl + R) * p.px + XO + xl;
+            T *dst0 = reinterpret_cast<T *>(q.base) + (long long)(zl + dz + R) * q.plane +
+                      (long long)(yl + dy + R) * q.px + XO + xl + dx;
+            const int rows = yh - yl, xw = xh - xl;
+            // rows of the box in chunks of 4 elements (the last may be short)
+            const int nch = (xw + 3) / 4;
+            const int units = (zh - zl) * rows * nch;
+            // whole chunks starting on 4-element boundaries on both sides:
+            // vector units (all of them, except at x cuts off that grid)
+            const bool vec = (xw & 3) == 0 && ((XO + xl) & 3) == 0 &&
+                             ((XO + xl + dx) & 3) == 0;
+            for (int u0 = tid; u0 < units; u0 += B * C::NT) {
+                Vec4 v[B];
+                T *d[B];
+                const T *sp[B];
+                int n[B];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) m |= (x + i >= nx - R ? 1u : 0u) << i;
-            put_row(1, x - nx, y, z, so, m & valid);
+                for (int k = 0; k < B; ++k) {
+                    const int u = u0 + k * C::NT;
+                    d[k] = nullptr;
+                    sp[k] = nullptr;
+                    n[k] = 0;
+                    if (u < units) {
+                        const int ch = u % nch, row = u / nch;
+                        const int y = row % rows, z = row / rows;
+                        sp[k] = src0 + (size_t)z * p.plane + (size_t)y * p.px + 4 * ch;
+                        d[k] = dst0 + (long long)z * q.plane + (long long)y * q.px + 4 * ch;
+                        n[k] = min(4, xw - 4 * ch);
+                        if (vec) v[k].load(sp[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    if (!d[k]) continue;
+                    if (vec) v[k].store(d[k]);
+                    else
+                        for (int i = 0; i < n[k]; ++i) d[k][i] = sp[k][i];
+                }
+            }
         }
     }
 
@@ -1032,21 +1076,31 @@ struct Step {
                 begin_item(it);
                 fill_one<0>(); fill_one<1>(); fill_one<2>(); fill_one<3>();
                 fill_one<4>(); fill_one<5>(); fill_one<6>(); fill_one<7>();
-                // five loop bodies, so that each item runs the smallest
+                // three loop bodies, so that each item runs the smallest
                 // code that covers it (instruction fetch limits the loop):
-                // whole tiles with neither puts nor sources/receivers,
-                // whole tiles with sources/receivers on some planes, whole
-                // tiles with puts, partial tiles without puts, and the
-                // general one.  Folding the puts into the first body as a
-                // runtime check cost 7 % at 512^3; source code in the put
-                // body cost 5-11 % on 2x2x2 runs; partial tiles on the
-                // general body cost 16 % at 1200^3; the source/receiver
-                // code in the main body cost 7-9 % with 16-bit storage.
-                if (fast_ && !item_puts && nl_ == 0) z_loop<true, false, false>(z1 - z0);
-                else if (fast_ && !item_puts) z_loop<true, false, true>(z1 - z0);
-                else if (fast_ && nl_ == 0) z_loop<true, true, false>(z1 - z0);
-                else if (!item_puts) z_loop<false, false, true>(z1 - z0);
-                else z_loop<false, true, true>(z1 - z0);
+                // whole tiles without sources/receivers, whole tiles with
+                // sources/receivers on some planes, and partial tiles.  The
+                // source/receiver code in the main body cost 7-9 % with
+                // 16-bit storage; partial tiles on a body with per-row
+                // checks and per-point masks everywhere cost 16 % at 1200^3.
+                // Halo puts run after the loop (put_item).
+                if (fast_ && nl_ == 0) z_loop<true, false>(z1 - z0);
+                else if (fast_) z_loop<true, true>(z1 - z0);
+                else z_loop<false, true>(z1 - z0);
+                if (item_puts) {           // uniform over the CTA
+                    consumer_sync(C::NT);
+                    PutItem p;
+                    p.u = unext;
+                    p.nbr = nbrput();
+                    p.plane = plane_;
+                    p.px = px_;
+                    p.x0 = x0; p.y0 = y0; p.z0 = z0; p.z1 = z1;
+                    p.nx = nx; p.ny = ny; p.nz = nz;
+                    p.has = 0;
+#pragma unroll
+                    for (int f = 0; f < 6; ++f) p.has |= (nbr_[f] >= 0 ? 1 : 0) << f;
+                    put_item(p, tid);
+                }
                 end_item(it);
             }
             if (k + 1 < A.nk) {
