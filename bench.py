@@ -537,7 +537,10 @@ def run_ours(args, world, rank, local, pg):
         variants[f"cannon_{CANNON_N}_p{CANNON_P}"] = run_cannon(device=local)
         variants[f"f32_{MINIMOD_N}cubed"] = run_minimod_size(device=local)
         for dt in ("f32", "bf16"):
-            for suffix, kw in (("", {}), ("_persistent", dict(persistent=True))):
+            # persistent: one tile for every shot (the autotuner's best
+            # uniform choice), so that one cooperative launch per 25-step
+            # chunk advances all 64 shots
+            for suffix, kw in (("", {}), ("_persistent", dict(persistent=True, margin=1.0))):
                 r = run_batch(dt, **kw)
                 variants[f"batch64_{dt}{suffix}"] = {
                     k: r[k] for k in ("gpts", "ms", "steps", "chunk",
@@ -804,6 +807,7 @@ def run_batch_modes(args):
     for dt in ("f32", "bf16"):
         for name, kw in (("batch_graphs_tuned_side_by_side", {}),
                          ("batch_persistent_tuned", dict(persistent=True)),
+                         ("batch_persistent_uniform_tile", dict(persistent=True, margin=1.0)),
                          ("batch_graphs_uniform_tile", dict(margin=1.0)),
                          ("batch_graphs_tile_model", dict(tiles_by="model")),
                          ("batch_graphs_default_tile", dict(autotune=False)),

@@ -102,8 +102,11 @@ def _seg_bytes(dtype):
 
 @pytest.mark.parametrize("dtype,mode", [
     ("f32", "graphs"), ("f32", "plain"), ("f32", "persistent"),
-    ("bf16", "graphs"), ("f16s", "persistent"), ("f64", "graphs")])
+    ("bf16", "graphs"), ("bf16", "persistent"), ("f16s", "persistent"),
+    ("f64", "graphs")])
 def test_batched_shots_match_alone(dtype, mode):
+    """Three groups (two tiles, with and without the sponge): side by side
+    on forked streams, or one cooperative launch per group and chunk."""
     ensure_built()
     alone = []
     with Segment(2 * _seg_bytes(dtype), nranks=2) as seg:
@@ -258,3 +261,32 @@ def test_autotune_picks_an_available_tile_and_caches_it():
             s.step(4)
             s.sync()
             assert s.info["tile"] == t1
+
+
+def test_persistent_batch_with_a_one_row_per_thread_tile():
+    """A persistent batch whose groups include a two-CTAs-per-SM tile
+    (128 x 7, one row per thread) next to the default one: each group's
+    cooperative launch covers its own occupancy; results are those of the
+    shots alone."""
+    ensure_built()
+    specs = [(48, 48, 48, 1, 1, 1, 8, 0), (64, 40, 56, 1, 1, 1, 8, 7)]
+    alone = []
+    with Segment(2 * _seg_bytes("f32")) as seg:
+        for k, spec in enumerate(specs):
+            with _make(seg, k, spec, "f32") as s:
+                s.step(STEPS)
+                s.sync()
+                alone.append(_result(s))
+        shots = [_make(seg, k, spec, "f32") for k, spec in enumerate(specs)]
+        try:
+            with Batch(seg, shots, persistent=True) as b:
+                assert b.info["groups"] == 2
+                b.step(STEPS)
+                shots[0].sync()
+            for k, s in enumerate(shots):
+                r = _result(s)
+                assert np.array_equal(r["u"], alone[k]["u"]), k
+                assert np.array_equal(r["traces"], alone[k]["traces"]), k
+        finally:
+            for s in shots:
+                s.close()
