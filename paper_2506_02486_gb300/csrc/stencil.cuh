@@ -301,6 +301,11 @@ struct Step {
 
     // consumer
     unsigned tg, jg;           // u loads / pointwise planes consumed
+    // their ring positions, kept as running counters (the ring depths need
+    // not be powers of two, and a division per use costs instructions in
+    // the loop): tg % SU and (tg / SU) & 1, (tg - R) % SU, jg % SP and
+    // (jg / SP) & 1
+    unsigned us, uph, cs, pss, pph;
     int kk;                    // step index within the chunk being computed
     bool aborted;              // a wait of this thread gave up
 
@@ -746,20 +751,32 @@ struct Step {
     // one that arrives; the arriving plane lands in entry 8 + P (P = phase
     // within a trip of KP planes) and the compute plane is the one 4 back.
 
+    // one more u plane consumed: tg and its ring position
+    __device__ __forceinline__ void advance_u()
+    {
+        ++tg;
+        if (++us == SU) {
+            us = 0;
+            uph ^= 1u;
+        }
+    }
+
     // Fill: the item's first 8 planes (interior z0 - 4 .. z0 + 3) only enter
     // the queue.  Each plane load is handed back 4 loads later.
     template <int QI>
     __device__ __forceinline__ void fill_one()
     {
-        unsigned slot = tg % SU;
-        wait_or_abort(ufull(slot), (tg / SU) & 1u);
-        const T *pl = ubuf(slot);
+        wait_or_abort(ufull(us), uph);
+        const T *pl = ubuf(us);
 #pragma unroll
         for (int r = 0; r < PY; ++r)
             ld_grp<T, PK>(pl + (PY * ty + r + R) * C::RW + HL + 4 * tx, Q[QI][r]);
         __syncwarp();
-        if (lane == 0 && tg >= R) mbar_arrive(uempty((tg - R) % SU));
-        ++tg;
+        if (tg >= R) {
+            if (lane == 0) mbar_arrive(uempty(cs));
+            cs = cs + 1 == SU ? 0 : cs + 1;
+        }
+        advance_u();
     }
 
     // One compute plane z.  FAST: a whole tile (every row and point valid)
@@ -769,7 +786,7 @@ struct Step {
     {
         // (1) x/y neighbours from the compute plane, staged R loads ago (its
         // full barrier was waited on then): issued before the waits below
-        const T *pl = ubuf((tg - R) % SU);
+        const T *pl = ubuf(cs);
         G yv[PY + 8], lf[PY], rt[PY];
         // the thread's own rows of the compute plane are already in the
         // queue (entry R + P, the same bits); only the y neighbours load
@@ -786,16 +803,15 @@ struct Step {
         }
         // (2) the plane that arrives now: the z + 4 neighbours
         {
-            unsigned slot = tg % SU;
-            wait_or_abort(ufull(slot), (tg / SU) & 1u);
-            const T *pn = ubuf(slot);
+            wait_or_abort(ufull(us), uph);
+            const T *pn = ubuf(us);
 #pragma unroll
             for (int r = 0; r < PY; ++r)
                 ld_grp<T, PK>(pn + (PY * ty + r + R) * C::RW + HL + 4 * tx, Q[8 + P][r]);
         }
         // (3) the pointwise tiles of plane z
-        unsigned ps = jg % SP;
-        wait_or_abort(pfull(ps), (jg / SP) & 1u);
+        const unsigned ps = pss;
+        wait_or_abort(pfull(ps), pph);
         G pa[PY], cf[PY];
 #pragma unroll
         for (int r = 0; r < PY; ++r) {
@@ -867,11 +883,16 @@ struct Step {
         // the pointwise tiles
         __syncwarp();
         if (lane == 0) {
-            mbar_arrive(uempty((tg - R) % SU));
+            mbar_arrive(uempty(cs));
             mbar_arrive(pempty(ps));
         }
+        cs = cs + 1 == SU ? 0 : cs + 1;
+        if (++pss == SP) {
+            pss = 0;
+            pph ^= 1u;
+        }
         ++jg;
-        ++tg;
+        advance_u();
     }
 
     // point sources: lap += wavelet[n] at the source cell, in the stored
@@ -1070,6 +1091,7 @@ struct Step {
         ty = tid / C::NTX;
         aborted = false;
         tg = jg = 0;
+        us = uph = cs = pss = pph = 0;
         for (int k = 0; k < A.nk; ++k) {
             kk = A.k + k;
             for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
