@@ -551,10 +551,10 @@ def run_ours(args, world, rank, local, pg):
         precision = precision_results(500, device=local)
     serving = None
     if args.serving and args.variants:
-        # the first 200 requests of the serving stream at 0.7 of the 64-shot
-        # FP32 batch throughput measured above: p50/p99 latency beside the
-        # throughput numbers
-        srv = run_serve(200, device=local,
+        # the serving stream (2000 Poisson requests, real time, ~2.5 min) at
+        # 0.7 of the 64-shot FP32 batch throughput measured above: p50/p99
+        # latency beside the throughput numbers
+        srv = run_serve(args.serve_requests, device=local,
                         capacity_gpts=variants["batch64_f32"]["gpts"])
         serving = {k: srv[k] for k in (
             "requests", "rate_per_s", "offered_load", "capacity_gpts_assumed",
@@ -920,7 +920,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
-                    help="skip the 200-request serving replay of the default run")
+                    help="skip the serving replay of the default run")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the default run's serving replay")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline",
                     action="store_false")
     ap.add_argument("--no-precision", dest="precision_check", action="store_false",

@@ -472,10 +472,18 @@ int make_items(const std::vector<SubDev> &subs, const TileInfo &ti, int grid,
             int z0 = (int)((long long)s.nz * c / nzc);
             int z1 = (int)((long long)s.nz * (c + 1) / nzc);
             if (z1 <= z0) continue;
-            for (int y0 = 0; y0 < s.ny; y0 += TY)
-                for (int x0 = 0; x0 < s.nx; x0 += TX) {
+            const int ntx = (s.nx + TX - 1) / TX;
+            for (int y0 = 0, row = 0; y0 < s.ny; y0 += TY, ++row)
+                for (int x0 = 0, col = 0; x0 < s.nx; x0 += TX, ++col) {
                     Item it{sub_base + si, x0 | (y0 << 16), z0, z1};
-                    v.push_back({Key{s.gz0 + z0, si, y0, x0}, it});
+                    // within a tile row the columns start at (row mod ntx):
+                    // CTA b takes items b, b + grid, ..., and when grid is
+                    // a multiple of the row length a plain order would give
+                    // each CTA one fixed column -- every partial, edge or
+                    // halo-put tile of the grid on the same few CTAs
+                    // (1200^3: 5.6 against 4.9 ms per step)
+                    const int key = (col + ntx - row % ntx) % ntx;
+                    v.push_back({Key{s.gz0 + z0, si, y0, key}, it});
                 }
         }
     }
