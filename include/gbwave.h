@@ -113,7 +113,20 @@ typedef struct {
                               CTAs wait for each other between steps (a
                               bounded device-wide barrier; cooperative
                               launch); needs GW_HALO_FUSED                */
+    int schedule;          /* work items to CTAs: GW_SCHED_AUTO (0),
+                              GW_SCHED_STATIC or GW_SCHED_DYNAMIC; the same
+                              results with every choice                   */
 } gw_shot_desc;
+
+/* How a launch's CTAs share the work items of a step.  STATIC: CTA b takes
+ * items b, b + grid, ... (balanced when the items are alike and there are
+ * few per CTA; CTAs on neighbouring tiles stay in step).  DYNAMIC: the CTAs
+ * take the items in order from a shared ticket counter (a CTA held up by a
+ * costlier item -- a partial tile, halo puts, sources -- takes fewer).
+ * AUTO: STATIC for an undecomposed shot with fewer than 16 items per CTA,
+ * DYNAMIC otherwise.  Batches use DYNAMIC unless every shot asks for
+ * STATIC. */
+enum { GW_SCHED_AUTO = 0, GW_SCHED_STATIC = 1, GW_SCHED_DYNAMIC = 2 };
 
 typedef struct {
     double dt;             /* time step used (s)                          */
@@ -126,6 +139,7 @@ typedef struct {
     int items;             /* work items (tile columns x z-chunks)        */
     double scale_u, scale_w;
     size_t device_bytes;   /* segment bytes held by the domain            */
+    int schedule;          /* GW_SCHED_STATIC or GW_SCHED_DYNAMIC in use   */
 } gw_domain_info;
 
 typedef struct {

@@ -33,6 +33,8 @@ struct Group {
     char *d_maps = nullptr;
     double *d_partials = nullptr;
     unsigned *d_gbar = nullptr;
+    unsigned *d_ctr = nullptr;      // work-item tickets
+    bool dynamic = true;            // dynamic schedule unless every shot asks for static
     unsigned *err = nullptr;    // the first shot's device error word
     int grid = 0;
 };
@@ -112,6 +114,7 @@ gw_status build_group(gw_batch *b, Group &g)
     g.d_maps = m + o_maps;
     g.d_partials = reinterpret_cast<double *>(m + o_part);
     g.d_gbar = reinterpret_cast<unsigned *>(m + o_bar);
+    g.d_ctr = reinterpret_cast<unsigned *>(m + o_bar + 64);
     GW_TRY_CUDA(cudaMemcpy(g.d_subs, g.subs.data(), sizeof(SubDev) * nsub, cudaMemcpyHostToDevice));
     GW_TRY_CUDA(cudaMemcpy(g.d_shots, g.shots.data(), sizeof(ShotDev) * nsh, cudaMemcpyHostToDevice));
     GW_TRY_CUDA(cudaMemcpy(g.d_items, g.items.data(), sizeof(Item) * nit, cudaMemcpyHostToDevice));
@@ -121,7 +124,7 @@ gw_status build_group(gw_batch *b, Group &g)
         GW_TRY_CUDA(cudaMemcpy(g.d_maps + off, d->d_maps, bytes, cudaMemcpyDeviceToDevice));
         off += bytes;
     }
-    GW_TRY_CUDA(cudaMemset(g.d_gbar, 0, sizeof(unsigned)));
+    GW_TRY_CUDA(cudaMemset(g.d_gbar, 0, 128));           // barrier and tickets
     // the tables are in place before any launch on a non-blocking stream
     GW_TRY_CUDA(cudaStreamSynchronize(nullptr));
     g.err = g.doms[0]->d_err;
@@ -143,6 +146,8 @@ StepArgs group_args(gw_batch *b, Group &g, int k)
     a.k = k;
     a.nk = 1;
     a.gbar = g.d_gbar;
+    a.ctr = g.d_ctr;
+    a.dynamic = g.dynamic ? 1 : 0;
     a.symmetric = g.symmetric ? 1 : 0;
     a.fused_halo = g.separate ? 0 : 1;
     return a;
@@ -156,6 +161,8 @@ namespace {
 gw_status enqueue_group(gw_batch *b, Group &g, int nk, cudaStream_t s, bool timed,
                         bool count_steps)
 {
+    // work-item tickets from zero (a launch that gave up may leave them set)
+    GW_TRY_CUDA(cudaMemsetAsync(g.d_ctr, 0, sizeof(unsigned), s));
     auto launch = [&](StepArgs a, int steps) -> gw_status {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (timed) {
@@ -310,6 +317,11 @@ gw_status gw_batch_create(gw_ctx *c, int nshots, gw_domain *const *shots, int ch
             g->ti = d->ti;
         }
         g->doms.push_back(d);
+    }
+    for (Group &g : b->groups) {
+        bool all_static = true;
+        for (gw_domain *d : g.doms) all_static = all_static && d->desc.schedule == GW_SCHED_STATIC;
+        g.dynamic = !all_static;
     }
     for (Group &g : b->groups) {
         gw_status st = build_group(b, g);

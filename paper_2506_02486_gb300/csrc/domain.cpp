@@ -183,6 +183,14 @@ gw_status plan_schedule(gw_domain *d)
     build_items(d);
     if (d->nitems == 0) return fail(GW_ERR_ARG, "empty grid");
     d->grid = std::min(d->grid, d->nitems);
+    // work items to CTAs: static round robin for an undecomposed shot with
+    // few items per CTA (balanced when the items are alike, and the CTAs on
+    // neighbouring tiles stay in step: 512^3, 8 items per CTA, 1.6-2.8 %
+    // faster), dynamic otherwise (1200^3 15 %, 2 x 2 x 2 with fused halo
+    // puts 6 % faster)
+    const int sch = d->desc.schedule;
+    d->dynamic = sch == GW_SCHED_DYNAMIC ||
+                 (sch != GW_SCHED_STATIC && (d->nsub() > 1 || d->nitems >= 16 * d->grid));
     // items and the norm partials of one chunk
     if (d->g_items) drop_alloc(d, d->g_items);
     size_t ib = sizeof(Item) * d->nitems;
@@ -274,6 +282,8 @@ StepArgs step_args(gw_domain *d, int k)
     a.fused_halo = d->desc.halo_mode == GW_HALO_FUSED ? 1 : 0;
     a.nk = 1;
     a.gbar = d->d_gbar;
+    a.ctr = d->d_ctr;
+    a.dynamic = d->dynamic ? 1 : 0;
     return a;
 }
 
@@ -294,6 +304,10 @@ gw_status enqueue_chunk(gw_domain *d, int nk, cudaStream_t s, bool timed)
 {
     const bool sponge = d->desc.sponge > 0;
     const bool sep = d->desc.halo_mode == GW_HALO_SEPARATE && !d->halo.empty();
+    // the step kernel leaves its work-item tickets at zero after every step;
+    // a launch that gave up (GW_ERR_TIMEOUT) may not, so every chunk starts
+    // from zero
+    GW_TRY_CUDA(cudaMemsetAsync(d->d_ctr, 0, sizeof(unsigned), s));
     if (d->desc.persistent && !sep && nk > 1) {
         // all nk steps in one launch, a device-wide barrier between steps
         GW_TRY_CUDA(cudaMemsetAsync(d->d_gbar, 0, sizeof(unsigned), s));
@@ -518,6 +532,8 @@ gw_status gw_domain_create(gw_ctx *c, const gw_shot_desc *desc, int px, int py,
     if (D.nx > 65535 || D.ny > 65535)
         return fail(GW_ERR_ARG, "nx, ny must be < 65536");
     if (D.dtype < DT_F32 || D.dtype > DT_BF16) return fail(GW_ERR_ARG, "bad dtype");
+    if (D.schedule < GW_SCHED_AUTO || D.schedule > GW_SCHED_DYNAMIC)
+        return fail(GW_ERR_ARG, "bad schedule %d", D.schedule);
     for (double sc : {D.scale_u, D.scale_w}) {
         int e2 = 0;
         // the kernels fold the scales into exact power-of-two factors
@@ -669,6 +685,7 @@ gw_status gw_domain_create(gw_ctx *c, const gw_shot_desc *desc, int px, int py,
     d->d_err = reinterpret_cast<unsigned *>(m + off_err);
     d->d_step = reinterpret_cast<int *>(m + off_step);
     d->d_gbar = reinterpret_cast<unsigned *>(m + off_err + 32);
+    d->d_ctr = reinterpret_cast<unsigned *>(m + off_err + 96);
     d->d_scratch = reinterpret_cast<double *>(m + off_scr);
     d->d_wavelet = reinterpret_cast<double *>(m + off_wl);
     d->d_norms = reinterpret_cast<double *>(m + off_norm);
@@ -755,6 +772,7 @@ gw_status gw_domain_info_get(gw_domain *d, gw_domain_info *out)
     out->scale_u = d->su;
     out->scale_w = d->sw;
     out->device_bytes = d->device_bytes;
+    out->schedule = d->dynamic ? GW_SCHED_DYNAMIC : GW_SCHED_STATIC;
     return GW_OK;
 }
 

@@ -43,6 +43,8 @@ struct gw_domain {
     unsigned *d_err = nullptr;
     int *d_step = nullptr;
     unsigned *d_gbar = nullptr;           // barrier of persistent launches
+    unsigned *d_ctr = nullptr;            // work-item tickets of the step kernel
+    bool dynamic = false;                 // dynamic work-item schedule
     double *d_scratch = nullptr;          // 4 doubles for checks
     double *d_chk = nullptr;              // 3 per-plane check partials per z
     double *d_wavelet = nullptr;

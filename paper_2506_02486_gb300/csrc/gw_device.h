@@ -92,6 +92,9 @@ struct StepArgs {
     int k;                 // step index within the chunk of the first step
     int nk;                // steps this launch performs (persistent: > 1)
     unsigned *gbar;        // device-wide barrier counter (zero at launch)
+    unsigned *ctr;         // work-item tickets (zero between steps; the
+                           // kernel resets it after each step)
+    int dynamic;           // 1: CTAs take items from ctr; 0: b, b + grid, ...
     int symmetric;         // 1: neighbour address = own + (dr * stride)
     int fused_halo;        // 1: epilogue stores into neighbours' halos
 };

@@ -189,7 +189,11 @@ struct Cfg {
     static constexpr int OFF_MISC = OFF_LOC + 16 * kMaxLocal;
     static constexpr int OFF_RED = OFF_MISC + 16;
     static constexpr int OFF_NBR = OFF_RED + 8 * NCW;     // 6 x NbrPut (32 B)
-    static constexpr int SMEM = OFF_NBR + 32 * 6;
+    // work-item ring from the producer to the consumers: IQ item indices,
+    // then IQ full and IQ empty mbarriers
+    static constexpr int IQ = 4;
+    static constexpr int OFF_IQ = OFF_NBR + 32 * 6;
+    static constexpr int SMEM = OFF_IQ + 4 * IQ + 16 * IQ;
     static_assert(TX % 4 == 0 && TY % PY == 0 && NT % 32 == 0, "tile");
     static_assert((RW * (int)sizeof(T)) % 16 == 0, "TMA box row");
     static_assert(SU >= 6 && SP >= 2, "ring depth");
@@ -306,6 +310,7 @@ struct Step {
     // the loop): tg % SU and (tg / SU) & 1, (tg - R) % SU, jg % SP and
     // (jg / SP) & 1
     unsigned us, uph, cs, pss, pph;
+    unsigned itn_;             // work items taken from the ring
     int kk;                    // step index within the chunk being computed
     bool aborted;              // a wait of this thread gave up
 
@@ -374,6 +379,69 @@ struct Step {
     __device__ volatile int *abortf() { return misc() + 1; }
     __device__ double *red() { return reinterpret_cast<double *>(smem + C::OFF_RED); }
     __device__ NbrPut *nbrput() { return reinterpret_cast<NbrPut *>(smem + C::OFF_NBR); }
+    __device__ volatile int *itemq() { return reinterpret_cast<volatile int *>(smem + C::OFF_IQ); }
+    __device__ uint64_t *iqfull(unsigned s)
+    {
+        return reinterpret_cast<uint64_t *>(smem + C::OFF_IQ + 4 * C::IQ) + s;
+    }
+    __device__ uint64_t *iqempty(unsigned s) { return iqfull(0) + C::IQ + s; }
+
+    // ---- work items ---------------------------------------------------
+    // Static schedule (A.dynamic == 0): CTA b takes items b, b + grid, ....
+    // Dynamic schedule: the CTAs take a step's items in order from a ticket
+    // counter (A.ctr, zero at the start of every step); every CTA draws
+    // tickets until it gets one past the last item, so a step hands out
+    // exactly nitems + gridDim.x tickets, and the CTA that draws the last
+    // one resets the counter for the next step.  A CTA held up by a costly
+    // item (a partial tile, halo puts, sources) takes fewer, and the CTAs
+    // running at the same time stay on neighbouring tiles.  Either way the
+    // producer claims the items (it streams ahead) and hands their indices
+    // to the consumers through a ring of IQ slots.
+    __device__ __forceinline__ int claim_item(unsigned &nth)
+    {
+        if (!A.dynamic) {
+            const unsigned t = blockIdx.x + gridDim.x * nth++;
+            if (t < (unsigned)A.nitems) return (int)t;
+            nth = 0;
+            return -1;
+        }
+        const unsigned t = atomicAdd(A.ctr, 1u);
+        if (t == (unsigned)A.nitems + gridDim.x - 1u) atomicExch(A.ctr, 0u);
+        return t < (unsigned)A.nitems ? (int)t : -1;
+    }
+
+    // producer: item index (-1: none left in this step) into slot q % IQ
+    __device__ __forceinline__ bool publish_item(int v, unsigned &q)
+    {
+        const unsigned s = q % C::IQ;
+        if (q >= (unsigned)C::IQ && !wait_slot(iqempty(s), ((q / C::IQ) - 1) & 1u, abortf()))
+            return false;
+        itemq()[s] = v;
+        mbar_arrive(iqfull(s));       // release: the index is visible to the waiter
+        ++q;
+        return true;
+    }
+
+    // consumers: the next item of this step, the same value in every
+    // consumer thread (-1: the step is done; -2: this CTA gave up).  One
+    // thread takes it from the ring and the consumer barrier broadcasts it,
+    // so that all consumer threads always take the same path.
+    __device__ __forceinline__ int next_item()
+    {
+        if (tid == 0) {
+            const unsigned s = itn_ % C::IQ;
+            int v = -2;
+            if (wait_slot(iqfull(s), (itn_ / C::IQ) & 1u, abortf())) {
+                v = itemq()[s];
+                mbar_arrive(iqempty(s));
+            }
+            misc()[2] = v;
+        }
+        ++itn_;
+        consumer_sync(C::NT);
+        return misc()[2];
+    }
+
 
     __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity)
     {
@@ -398,7 +466,7 @@ struct Step {
         // the same CTA a few microseconds after it is read).
         const uint64_t pol_u = policy_evict_normal();
         const uint64_t pol_p = policy_evict_normal();
-        unsigned L = 0, P = 0;
+        unsigned L = 0, P = 0, iqn = 0, nth = 0;
         for (int k = 0; k < A.nk; ++k) {
         if (k > 0) {
             // the previous step's stores must be complete everywhere before
@@ -410,7 +478,13 @@ struct Step {
             }
             fence_proxy_async_global();
         }
-        for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
+        for (;;) {
+            const int it = claim_item(nth);
+            if (!publish_item(it, iqn)) {
+                *abortf() = 1;
+                goto drain;
+            }
+            if (it < 0) break;
             const Item I = A.items[it];
             const SubDev &s = A.subs[I.sub];
             const int p = (*A.shots[s.shot].step + A.k + k) & 1;
@@ -1079,6 +1153,10 @@ struct Step {
                 mbar_init(pfull(q), 1);
                 mbar_init(pempty(q), C::NCW);
             }
+            for (int q = 0; q < C::IQ; ++q) {
+                mbar_init(iqfull(q), 1);
+                mbar_init(iqempty(q), 1);
+            }
             misc()[1] = 0;
             fence_barrier_init();
         }
@@ -1092,9 +1170,13 @@ struct Step {
         aborted = false;
         tg = jg = 0;
         us = uph = cs = pss = pph = 0;
+        itn_ = 0;
         for (int k = 0; k < A.nk; ++k) {
             kk = A.k + k;
-            for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
+            for (;;) {
+                const int it = next_item();
+                if (it == -2) return;      // this CTA gave up (error bit set)
+                if (it < 0) break;
                 begin_item(it);
                 fill_one<0>(); fill_one<1>(); fill_one<2>(); fill_one<3>();
                 fill_one<4>(); fill_one<5>(); fill_one<6>(); fill_one<7>();

@@ -31,6 +31,7 @@ GW_ERR_NOMEM = -8
 
 GW_F32, GW_F64, GW_F16S, GW_BF16 = 0, 1, 2, 3
 GW_HALO_FUSED, GW_HALO_SEPARATE = 0, 1
+GW_SCHED_AUTO, GW_SCHED_STATIC, GW_SCHED_DYNAMIC = 0, 1, 2
 GW_FIELD_U, GW_FIELD_UPREV, GW_FIELD_W, GW_FIELD_COEF = 0, 1, 2, 3
 
 DTYPES = {"f32": GW_F32, "f64": GW_F64, "f16s": GW_F16S, "bf16": GW_BF16}
@@ -52,7 +53,7 @@ class gw_shot_desc(ctypes.Structure):
         ("halo_mode", ctypes.c_int), ("chunk", ctypes.c_int),
         ("tile", ctypes.c_int), ("zchunk", ctypes.c_int),
         ("scale_u", ctypes.c_double), ("scale_w", ctypes.c_double),
-        ("persistent", ctypes.c_int),
+        ("persistent", ctypes.c_int), ("schedule", ctypes.c_int),
     ]
 
 
@@ -63,7 +64,7 @@ class gw_domain_info(ctypes.Structure):
         ("step", ctypes.c_int), ("tile", ctypes.c_int),
         ("ctas", ctypes.c_int), ("items", ctypes.c_int),
         ("scale_u", ctypes.c_double), ("scale_w", ctypes.c_double),
-        ("device_bytes", ctypes.c_size_t),
+        ("device_bytes", ctypes.c_size_t), ("schedule", ctypes.c_int),
     ]
 
 
@@ -469,7 +470,8 @@ def gw_cannon_stats(cn: int) -> dict:
 def shot_desc(nx, ny, nz, *, h=10.0, courant=0.0, dt=0.0, nsteps=0,
               dtype="f32", sponge=0, sponge_a=0.0, periodic=0,
               halo_mode=GW_HALO_FUSED, chunk=0, tile=0, zchunk=0,
-              scale_u=0.0, scale_w=0.0, persistent=0) -> gw_shot_desc:
+              scale_u=0.0, scale_w=0.0, persistent=0,
+              schedule=0) -> gw_shot_desc:
     d = gw_shot_desc()
     d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
     d.h, d.courant, d.dt = float(h), float(courant), float(dt)
@@ -480,6 +482,7 @@ def shot_desc(nx, ny, nz, *, h=10.0, courant=0.0, dt=0.0, nsteps=0,
     d.chunk, d.tile, d.zchunk = int(chunk), int(tile), int(zchunk)
     d.scale_u, d.scale_w = float(scale_u), float(scale_w)
     d.persistent = int(persistent)
+    d.schedule = int(schedule)
     return d
 
 

@@ -39,18 +39,22 @@ def test_undecomposed_reference_matches_oracle(reference):
 
 def test_persistent_chunks_are_bitwise(reference):
     """K steps in one launch (device-wide barrier between steps) give the
-    bits of one launch per step, undecomposed and 2 x 2 x 2."""
+    bits of one launch per step, undecomposed and 2 x 2 x 2, with the static
+    and the dynamic work-item schedule (the dynamic one hands out a step's
+    tickets and resets its counter between the steps of one launch)."""
     vel, src, rec, base = reference
-    for dec in ((1, 1, 1), (2, 2, 2)):
+    for dec, sched in (((1, 1, 1), 0), ((1, 1, 1), 2), ((2, 2, 2), 0), ((2, 2, 2), 1)):
         g = gpu_run(vel, 60, src=src, f_peak=40.0, receivers=rec, sponge=10,
-                    px=dec[0], py=dec[1], pz=dec[2], persistent=1, chunk=7)
-        assert np.array_equal(g["u32"], base["u32"])
-        assert np.array_equal(g["traces"], base["traces"])
+                    px=dec[0], py=dec[1], pz=dec[2], persistent=1, chunk=7,
+                    schedule=sched)
+        assert np.array_equal(g["u32"], base["u32"]), (dec, sched)
+        assert np.array_equal(g["traces"], base["traces"]), (dec, sched)
 
 
 @pytest.mark.parametrize("px,py,pz,symmetric,mode,split", [
     (2, 2, 2, True, gw.GW_HALO_FUSED, (None, None, None)),
     (2, 2, 2, True, gw.GW_HALO_SEPARATE, (None, None, None)),
+    (2, 2, 2, "static", gw.GW_HALO_FUSED, (None, None, None)),
     (4, 1, 1, True, gw.GW_HALO_FUSED, (None, None, None)),   # x slabs
     (1, 1, 6, False, gw.GW_HALO_FUSED, (None, None, None)),
     (3, 2, 1, False, gw.GW_HALO_FUSED, ([20, 41, 35], [30, 50], None)),
@@ -59,11 +63,15 @@ def test_persistent_chunks_are_bitwise(reference):
 ])
 def test_decomposed_equals_undecomposed(reference, px, py, pz, symmetric,
                                         mode, split):
+    """Decomposed shots take the dynamic work-item schedule unless asked
+    (the "static" case: symmetric, static round robin)."""
     vel, src, rec, base = reference
+    sched = gw.GW_SCHED_STATIC if symmetric == "static" else gw.GW_SCHED_AUTO
     g = gpu_run(vel, 60, src=src, f_peak=40.0, receivers=rec, sponge=10,
-                px=px, py=py, pz=pz, symmetric=symmetric, halo_mode=mode,
-                split=split)
+                px=px, py=py, pz=pz, symmetric=bool(symmetric), halo_mode=mode,
+                split=split, schedule=sched)
     assert g["info"]["nsub"] == px * py * pz
+    assert g["info"]["schedule"] == (gw.GW_SCHED_STATIC if sched else gw.GW_SCHED_DYNAMIC)
     assert np.array_equal(g["u32"], base["u32"])
     assert np.array_equal(g["traces"], base["traces"])
     # norms: per-thread, per-plane FP32 partials of at most 8 positive

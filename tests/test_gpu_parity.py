@@ -67,16 +67,24 @@ def test_ragged_layered_sponge_matches_oracle(tile):
     assert_close(g["traces"], o["traces"], TOL32, "traces")
 
 
-def test_tiles_and_graphs_do_not_change_bits():
+def test_tiles_graphs_and_schedules_do_not_change_bits():
+    """Tiles, z-chunking, graph or plain launches, persistent launches and
+    the static or dynamic work-item schedule: the same bits."""
     nx, ny, nz = 70, 45, 33
     vel = workloads.layered(nx, ny, nz, seed=3)
     src = (30, 20, 16)
-    runs = [gpu_run(vel, 37, src=src, f_peak=25.0, sponge=5, tile=t,
-                    chunk=c, zchunk=z)
-            for t, c, z in [(1, 0, 0), (2, 7, 5), (3, -1, 0), (4, 4, 13),
-                            (1, 25, 33)]]
-    for r in runs[1:]:
-        assert np.array_equal(r["u32"], runs[0]["u32"])
+    cases = [(1, 0, 0, 0, 0), (2, 7, 5, 2, 0), (3, -1, 0, 1, 0), (4, 4, 13, 2, 0),
+             (1, 25, 33, 1, 0), (1, 6, 5, 2, 1), (2, 9, 7, 1, 1), (5, -1, 3, 2, 0)]
+    runs = [gpu_run(vel, 37, src=src, f_peak=25.0, sponge=5, tile=t, chunk=c,
+                    zchunk=z, schedule=sch, persistent=p)
+            for t, c, z, sch, p in cases]
+    for (t, c, z, sch, p), r in zip(cases, runs):
+        assert np.array_equal(r["u32"], runs[0]["u32"]), (t, c, z, sch, p)
+        if sch:
+            assert r["info"]["schedule"] == sch
+        # norms: each thread's plane partials depend on the tile (gamma_7)
+        assert r["norms"] == pytest.approx(runs[0]["norms"],
+                                           rel=2 * (gamma(7) + gamma(127) ** 2))
 
 
 @pytest.mark.parametrize("dtype,tiles", [("f16s", [1, 2, 3, 4, 5]),
