@@ -339,6 +339,12 @@ gw_status gw_ctx_destroy(gw_ctx *c)
         cudaSetDevice(c->device);
         c->pool.destroy();      // streams with pending work finish first
         for (cudaEvent_t ev : c->pool_events) cudaEventDestroy(ev);
+        if (c->up_stream) {
+            cudaStreamSynchronize(c->up_stream);
+            cudaStreamDestroy(c->up_stream);
+        }
+        for (cudaEvent_t ev : c->up_ev)
+            if (ev) cudaEventDestroy(ev);
     }
     delete c;
     return GW_OK;

@@ -87,7 +87,25 @@ __global__ void k_coef(ModelSlab m, SubDev sd, int xo)
                                : ((size_t)(gz - m.z_lo) * m.NY + (size_t)(sd.gy0 + y)) * m.NX +
                                      (size_t)(sd.gx0 + x);
         double nu = (double)v[src] * m.dt_over_h;   // FP64 precompute
-        c[pidx(sd, xo, x, y, gz - sd.gz0)] = from_d<CT>(nu * nu);
+        c[pidx(sd, xo, x, y, gz - sd.gz0)] = from_d<CT>(m.raw ? (double)v[src] : nu * nu);
+    }
+}
+
+// coef = (v dt / h)^2 over a subdomain whose coef array holds v (exactly:
+// only used when the coef type holds the input velocities without rounding)
+template <class CT>
+__global__ void k_coef_square(SubDev sd, int xo, double dt_over_h)
+{
+    CT *c = reinterpret_cast<CT *>(sd.coef);
+    const size_t npl = (size_t)sd.nx * sd.ny, n = npl * (size_t)sd.nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % sd.nx);
+        const int y = (int)((i / sd.nx) % sd.ny);
+        const int z = (int)(i / npl);
+        CT &e = c[pidx(sd, xo, x, y, z)];
+        const double nu = to_d<CT>(e) * dt_over_h;   // FP64 precompute
+        e = from_d<CT>(nu * nu);
     }
 }
 
@@ -95,6 +113,19 @@ static int grid_for(size_t n)
 {
     size_t g = (n + 255) / 256;
     return (int)(g > 8192 ? 8192 : (g ? g : 1));
+}
+
+cudaError_t launch_coef_square(const SubDev &sd, int dtype, double dt_over_h,
+                               cudaStream_t s)
+{
+    const int g = grid_for((size_t)sd.nx * sd.ny * (size_t)sd.nz);
+    const int xo = dtype_xoff(dtype);
+    switch (dtype) {
+    case DT_F32: k_coef_square<float><<<g, 256, 0, s>>>(sd, xo, dt_over_h); break;
+    case DT_F64: k_coef_square<double><<<g, 256, 0, s>>>(sd, xo, dt_over_h); break;
+    default: return cudaErrorInvalidValue;   // FP16 coef cannot hold v exactly
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_coef(const ModelSlab &m, const SubDev &sd, int dtype,

@@ -424,6 +424,42 @@ gw_status stage_alloc(gw_domain *d, Stage &st, size_t want, size_t plane_bytes)
     return local_alloc(d, st.bytes, &st.p, &st.g);
 }
 
+// Host slabs of planes through the two halves of a staging buffer: the
+// copy of slab i + 1 runs on the context's copy stream while the kernels of
+// slab i run on the legacy stream (pinned host memory: ~210 GB/s on GB300's
+// host link, so the kernels hide behind the copies).  consume(buf, z0, z1)
+// enqueues the kernels for planes [z0, z1) staged at buf.
+template <class F>
+gw_status upload_slabs(gw_domain *d, const Stage &st, const char *h, size_t plane_bytes,
+                              F &&consume)
+{
+    gw_ctx *c = d->ctx;
+    if (!c->up_stream) {
+        GW_TRY_CUDA(cudaStreamCreateWithFlags(&c->up_stream, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : c->up_ev)
+            GW_TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    const size_t half = (st.bytes - 16) / 2 / kAlign * kAlign;
+    const int nz = d->desc.nz;
+    const int pps = (int)std::max<size_t>(1, half / plane_bytes);
+    const bool two = half >= plane_bytes;       // else one slab at a time
+    for (int i = 0, z = 0; z < nz; ++i, z += pps) {
+        const int zh = std::min(nz, z + pps);
+        const int b = two ? (i & 1) : 0;
+        char *buf = st.p + (size_t)b * half;
+        cudaEvent_t copied = c->up_ev[2 * b], used = c->up_ev[2 * b + 1];
+        if (i >= (two ? 2 : 1)) GW_TRY_CUDA(cudaStreamWaitEvent(c->up_stream, used, 0));
+        GW_TRY_CUDA(cudaMemcpyAsync(buf, h + plane_bytes * (size_t)z,
+                                    plane_bytes * (size_t)(zh - z), cudaMemcpyHostToDevice,
+                                    c->up_stream));
+        GW_TRY_CUDA(cudaEventRecord(copied, c->up_stream));
+        GW_TRY_CUDA(cudaStreamWaitEvent(nullptr, copied, 0));
+        GW_TRY(consume(buf, z, zh));
+        GW_TRY_CUDA(cudaEventRecord(used, nullptr));
+    }
+    return GW_OK;
+}
+
 int planes_per_slab(const gw_domain *d, size_t bytes_per_elem, size_t stage)
 {
     size_t plane = (size_t)d->desc.nx * d->desc.ny * bytes_per_elem;
@@ -804,17 +840,26 @@ static gw_status set_model_impl(gw_domain *d, const void *vel, bool f32)
     const size_t plane = (size_t)D.nx * D.ny;
     Stage st;
     GW_TRY(stage_alloc(d, st, plane * D.nz * vs + 16, plane * vs));
-    int pps = planes_per_slab(d, vs, st.bytes - 16);
     unsigned long long *d_max = reinterpret_cast<unsigned long long *>(d->d_scratch);
     GW_TRY_CUDA(cudaMemset(d_max, 0, sizeof *d_max));
     const char *h = static_cast<const char *>(vel);
+    // When the coef array holds the input velocities exactly (FP32 coef and
+    // FP32 input, or FP64 coef), the model crosses to the device once: the
+    // first pass stores v in the coef array while it finds vmax, and coef =
+    // (v dt / h)^2 is then formed in place -- the same FP64 product of the
+    // same v, so the same bits as from the host copy.  Otherwise a second
+    // pass reads the host model again.
+    const bool once = d->dtype == DT_F64 || (d->dtype == DT_F32 && f32);
     // pass 1: vmax on the GPU
-    for (int z = 0; z < D.nz; z += pps) {
-        int zh = std::min(D.nz, z + pps);
-        size_t b = plane * (size_t)(zh - z) * vs;
-        GW_TRY_CUDA(cudaMemcpy(st.p, h + plane * (size_t)z * vs, b, cudaMemcpyHostToDevice));
-        GW_TRY_CUDA(launch_vmax(st.p, plane * (size_t)(zh - z), f32, d_max, nullptr));
-    }
+    GW_TRY(upload_slabs(d, st, h, plane * vs, [&](char *buf, int z, int zh) -> gw_status {
+        GW_TRY_CUDA(launch_vmax(buf, plane * (size_t)(zh - z), f32, d_max, nullptr));
+        if (once) {
+            ModelSlab ms{buf, f32 ? 1 : 0, D.nx, D.ny, z, zh, 0.0, 0, 1};
+            for (const SubDev &s : d->subs)
+                GW_TRY_CUDA(launch_coef(ms, s, d->dtype, nullptr));
+        }
+        return GW_OK;
+    }));
     unsigned long long bits = 0;
     GW_TRY_CUDA(cudaMemcpy(&bits, d_max, sizeof bits, cudaMemcpyDeviceToHost));
     double vmax;
@@ -822,14 +867,17 @@ static gw_status set_model_impl(gw_domain *d, const void *vel, bool f32)
     if (!(vmax > 0) || !std::isfinite(vmax))
         return fail(GW_ERR_ARG, "velocity model must be positive and finite");
     set_time_step(d, vmax);
-    // pass 2: coef = (v dt / h)^2 in FP64 on the GPU, rounded to storage
-    for (int z = 0; z < D.nz; z += pps) {
-        int zh = std::min(D.nz, z + pps);
-        size_t b = plane * (size_t)(zh - z) * vs;
-        GW_TRY_CUDA(cudaMemcpy(st.p, h + plane * (size_t)z * vs, b, cudaMemcpyHostToDevice));
-        ModelSlab ms{st.p, f32 ? 1 : 0, D.nx, D.ny, z, zh, d->dt / D.h, 0};
+    if (once) {
         for (const SubDev &s : d->subs)
-            GW_TRY_CUDA(launch_coef(ms, s, d->dtype, nullptr));
+            GW_TRY_CUDA(launch_coef_square(s, d->dtype, d->dt / D.h, nullptr));
+    } else {
+        // pass 2: coef = (v dt / h)^2 in FP64 on the GPU, rounded to storage
+        GW_TRY(upload_slabs(d, st, h, plane * vs, [&](char *buf, int z, int zh) -> gw_status {
+            ModelSlab ms{buf, f32 ? 1 : 0, D.nx, D.ny, z, zh, d->dt / D.h, 0, 0};
+            for (const SubDev &s : d->subs)
+                GW_TRY_CUDA(launch_coef(ms, s, d->dtype, nullptr));
+            return GW_OK;
+        }));
     }
     // the legacy stream only: work of other shots on other streams runs on
     GW_TRY_CUDA(cudaStreamSynchronize(nullptr));
@@ -1085,9 +1133,10 @@ gw_status gw_read_receivers(gw_domain *d, float *out, int nrec, int nsteps)
                     d->nrec, nsteps);
     std::lock_guard<std::recursive_mutex> lk(d->ctx->mu);
     GW_TRY(sync_dom(d));
-    for (int r = 0; r < nrec; ++r)
-        GW_TRY_CUDA(cudaMemcpy(out + (size_t)r * nsteps, d->d_traces + (size_t)r * d->shot.cap,
-                               sizeof(float) * nsteps, cudaMemcpyDeviceToHost));
+    if (nrec && nsteps)
+        GW_TRY_CUDA(cudaMemcpy2D(out, sizeof(float) * nsteps, d->d_traces,
+                                 sizeof(float) * d->shot.cap, sizeof(float) * nsteps, nrec,
+                                 cudaMemcpyDeviceToHost));
     return GW_OK;
 }
 

@@ -121,6 +121,10 @@ struct gw_ctx {
     int num_sms = 0;
     // autotuner results: shape/split/type key -> time per step of each tile
     std::map<std::string, std::vector<double>> tuned;   // ms per tile
+    // host -> device uploads of models (gw_set_model*): a copy stream and,
+    // per half of the staging buffer, "copied" and "used" events
+    cudaStream_t up_stream = nullptr;
+    cudaEvent_t up_ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
     char *rank_base(int r) const { return base + (size_t)r * rank_bytes; }
 };

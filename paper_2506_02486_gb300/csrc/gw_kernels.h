@@ -52,9 +52,14 @@ struct ModelSlab {
     int z_lo, z_hi;    // global planes in the slab
     double dt_over_h;
     int layered;       // 1: v holds one value per plane (v[z - z_lo])
+    int raw;           // 1: store v itself (rounded to the coef type)
 };
 cudaError_t launch_coef(const ModelSlab &m, const SubDev &sub, int dtype,
                         cudaStream_t s);
+// In place over a subdomain whose coef array holds velocities (stored by a
+// raw launch_coef): coef = (v dt / h)^2 in FP64, rounded to the coef type.
+cudaError_t launch_coef_square(const SubDev &sub, int dtype, double dt_over_h,
+                               cudaStream_t s);
 
 // Dense <-> padded transfers of a slab of planes of one field.
 // which: 0 = u[cur], 1 = u[cur^1], 2 = w, 3 = coef.  `scale` multiplies on

@@ -56,7 +56,9 @@ def homogeneous(nx: int, ny: int, nz: int, v: float = 1500.0) -> np.ndarray:
 def _layer_profile(nz: int, rng: np.random.Generator, nlayers: int,
                    vmin: float, vmax: float) -> np.ndarray:
     depths = np.sort(rng.uniform(0.0, float(nz), size=nlayers - 1))
-    vels = rng.uniform(vmin, vmax, size=nlayers)
+    # velocities rounded to FP32 values, so that a model passed in FP32 and
+    # the same model passed in FP64 are the same numbers
+    vels = rng.uniform(vmin, vmax, size=nlayers).astype(np.float32).astype(np.float64)
     k = np.arange(nz, dtype=np.float64)
     layer = np.searchsorted(depths, k, side="right")
     return vels[layer]
