@@ -88,7 +88,8 @@ gw_status build_group(gw_batch *b, Group &g)
         long long dp = (long long)d->desc.nx * d->desc.ny * d->desc.nz;
         int share = (int)std::max<long long>(1, (long long)G * dp / std::max(1LL, pts));
         std::vector<Item> it;
-        make_items(d->subs, g.ti, share, d->desc.zchunk, it, base);
+        make_items(d->subs, g.ti, share, d->desc.zchunk,
+                   g.dynamic ? GW_SCHED_DYNAMIC : GW_SCHED_STATIC, it, base);
         ShotDev sh = d->shot;
         sh.first_item = (int)g.items.size();
         sh.nitems = (int)it.size();

@@ -142,7 +142,7 @@ gw_status encode_map(gw_domain *d, CUtensorMap *out, char *base, const SubDev &s
 
 void build_items(gw_domain *d)
 {
-    d->zc = make_items(d->subs, d->ti, d->grid, d->desc.zchunk, d->items);
+    d->zc = make_items(d->subs, d->ti, d->grid, d->desc.zchunk, d->desc.schedule, d->items);
     d->nitems = (int)d->items.size();
 }
 
@@ -183,14 +183,13 @@ gw_status plan_schedule(gw_domain *d)
     build_items(d);
     if (d->nitems == 0) return fail(GW_ERR_ARG, "empty grid");
     d->grid = std::min(d->grid, d->nitems);
-    // work items to CTAs: static round robin for an undecomposed shot with
-    // few items per CTA (balanced when the items are alike, and the CTAs on
-    // neighbouring tiles stay in step: 512^3, 8 items per CTA, 1.6-2.8 %
-    // faster), dynamic otherwise (1200^3 15 %, 2 x 2 x 2 with fused halo
-    // puts 6 % faster)
-    const int sch = d->desc.schedule;
-    d->dynamic = sch == GW_SCHED_DYNAMIC ||
-                 (sch != GW_SCHED_STATIC && (d->nsub() > 1 || d->nitems >= 16 * d->grid));
+    // work items to CTAs: static round robin for an undecomposed shot
+    // whose tile columns fit in one round of CTAs (items alike, and the
+    // CTAs on neighbouring tiles stay in step: 512^3 1-3 % faster), dynamic
+    // otherwise (640^3 6.5 %, 1200^3 27 %, 2 x 2 x 2 with fused halo puts
+    // 6 % faster)
+    d->dynamic = dynamic_schedule(d->desc.schedule, d->nsub(), tile_columns(d->subs, d->ti),
+                                  d->grid);
     // items and the norm partials of one chunk
     if (d->g_items) drop_alloc(d, d->g_items);
     size_t ib = sizeof(Item) * d->nitems;
@@ -478,34 +477,53 @@ gw_status check_dom(gw_domain *d)
 
 namespace gw {
 
+long long tile_columns(const std::vector<SubDev> &subs, const TileInfo &ti)
+{
+    long long n = 0;
+    for (const SubDev &s : subs)
+        n += (long long)((s.nx + ti.tx - 1) / ti.tx) * ((s.ny + ti.ty - 1) / ti.ty);
+    return n;
+}
+
+bool dynamic_schedule(int sched, int nsub, long long ncols, int grid)
+{
+    if (sched == GW_SCHED_STATIC) return false;
+    if (sched == GW_SCHED_DYNAMIC) return true;
+    return nsub > 1 || ncols > grid;
+}
+
 // Work items in z-chunk-major order (CTAs running together hold
 // neighbouring columns at the same depth).
 int make_items(const std::vector<SubDev> &subs, const TileInfo &ti, int grid,
-               int zchunk, std::vector<Item> &items, int sub_base)
+               int zchunk, int sched, std::vector<Item> &items, int sub_base)
 {
     const int TX = ti.tx, TY = ti.ty;
-    long long ncols = 0;
+    const long long ncols = tile_columns(subs, ti);
     int nzmax = 0;
-    for (const SubDev &s : subs) {
-        ncols += (long long)((s.nx + TX - 1) / TX) * ((s.ny + TY - 1) / TY);
-        nzmax = std::max(nzmax, s.nz);
-    }
+    for (const SubDev &s : subs) nzmax = std::max(nzmax, s.nz);
     int zc = zchunk;
     if (zc <= 0) {
-        // Items of 16 to ti.zcap planes (measured on 512^3: 52-86-plane
-        // items run fastest, 64 best for FP32; 128 planes 3 % and one item
-        // per CTA 17 % slower), chosen to fill the last round of `grid`
-        // CTAs: cost = rounds * (planes + 8 * alpha), where a streamed-only
-        // halo plane costs alpha = 0.5 of a computed one.
-        double best = 1e300;
-        int best_n = 1;
-        const int cap = ti.zcap > 0 ? ti.zcap : 72;
-        const int lo = std::max(1, (nzmax + cap - 1) / cap);
+        // nzc chunks per column, for the lowest modelled step time.  An
+        // item costs its planes plus 8 * 0.7 (its z halo is streamed but
+        // not computed).  Static schedule: whole rounds of `grid` items.
+        // Dynamic: the work spread over `grid` CTAs plus ti.tail item times
+        // for the last, uneven round.  At least two chunks per column (one
+        // 512-plane item per column: 512^3 1-8 % slower than two), at
+        // least 16 planes per item, at most ti.zcap under the dynamic
+        // schedule.  Measured on 512^3 (static): 256-plane items 376
+        // against 353 Gpts/s with 64 for FP32.
+        const bool dyn = dynamic_schedule(sched, (int)subs.size(), ncols, grid);
+        const double halo = 8 * 0.7;
+        const int cap = dyn && ti.zcap > 0 ? ti.zcap : std::max(1, nzmax);
+        const int lo = std::max(nzmax >= 32 ? 2 : 1, (nzmax + cap - 1) / cap);
         const int hi = std::max(lo, nzmax / 16);
+        double best = 1e300;
+        int best_n = lo;
         for (int nzc = lo; nzc <= hi; ++nzc) {
-            long long n = ncols * nzc;
-            long long rounds = (n + grid - 1) / grid;
-            double cost = (double)rounds * ((double)nzmax / nzc + 8 * 0.5);
+            const double item = (double)nzmax / nzc + halo;
+            const long long n = ncols * nzc;
+            const double cost = dyn ? (double)n * item / grid + ti.tail * item
+                                    : (double)((n + grid - 1) / grid) * item;
             if (cost < best - 1e-9) {
                 best = cost;
                 best_n = nzc;

@@ -11,11 +11,18 @@
 namespace gw {
 constexpr int kDefaultChunk = 25;
 
+// Tile columns (ti.tx x ti.ty) of all of `subs`.
+long long tile_columns(const std::vector<SubDev> &subs, const TileInfo &ti);
+// The work-item schedule of a shot: `sched` (GW_SCHED_*) if it forces one,
+// else static for an undecomposed shot whose tile columns fit in one round
+// of `grid` CTAs and dynamic otherwise.
+bool dynamic_schedule(int sched, int nsub, long long ncols, int grid);
 // Work items of `subs` (subdomain indices offset by sub_base) for a tile of
 // ti.tx x ti.ty, z-chunk-major; zchunk <= 0 lets the cost model pick the
-// planes per item for `grid` CTAs.  Returns the planes per item used.
+// planes per item for `grid` CTAs under the schedule `sched` would give.
+// Returns the planes per item used.
 int make_items(const std::vector<SubDev> &subs, const TileInfo &ti, int grid,
-               int zchunk, std::vector<Item> &items, int sub_base = 0);
+               int zchunk, int sched, std::vector<Item> &items, int sub_base = 0);
 }  // namespace gw
 
 using gw::HaloDesc;

@@ -19,7 +19,9 @@ struct TileInfo {
     int tx, ty;        // tile extent in x and y (interior points)
     int threads;       // threads per CTA
     size_t smem;       // dynamic shared memory bytes
-    int zcap;          // most planes per work item
+    int zcap;          // most planes per work item under the dynamic schedule
+    double tail;       // dynamic schedule: cost of the last, uneven round of
+                       // items, in item times (the z-chunk cost model)
 };
 
 // Tile configurations available for a storage type (ids 0..n-1).

@@ -56,9 +56,14 @@ bool step_cfg_info(int dtype, int cfg, TileInfo *out)
     const Entry *e = find(dtype, cfg);
     if (!e) return false;
     *out = e->info();
-    // measured: FP32 tiles run best on ~64-plane items, the 16-bit ones on
-    // ~86 (1024 x 1024 x 512: 362 against 336 Gpts/s with 64)
-    out->zcap = dtype_size(dtype) == 2 ? 96 : 72;
+    // fitted to sweeps of the planes per item under the dynamic schedule
+    // (512^3 to 1200^3, 2 x 2 x 2): the 16-bit tiles keep gaining up to
+    // ~300-plane items (1200^3 BF16: 379.6 against 368.7 Gpts/s with 86),
+    // the FP32 ones are best at ~86-128 and lose 2-4 % at 300 as the
+    // last round of long items runs on part of the GPU
+    const bool two = dtype_size(dtype) == 2;
+    out->zcap = two ? 320 : 100;
+    out->tail = two ? 0.15 : 1.5;
     return true;
 }
 
