@@ -106,7 +106,9 @@ typedef struct {
                               graphs (plain launches)                     */
     int tile;              /* kernel tile configuration id + 1; 0: default */
     int zchunk;            /* planes per work item; 0: chosen by the cost
-                              model (load balance vs z-halo re-reads)     */
+                              model (load balance vs z-halo re-reads; at
+                              least two z-chunks per column, at most 512
+                              planes)                                     */
     double scale_u;        /* GW_F16S: power-of-two scale of u; 0: auto   */
     double scale_w;        /* GW_F16S: power-of-two scale of w; 0: auto   */
     int persistent;        /* != 0: each chunk of steps is one launch whose
@@ -123,9 +125,9 @@ typedef struct {
  * few per CTA; CTAs on neighbouring tiles stay in step).  DYNAMIC: the CTAs
  * take the items in order from a shared ticket counter (a CTA held up by a
  * costlier item -- a partial tile, halo puts, sources -- takes fewer).
- * AUTO: STATIC for an undecomposed shot with fewer than 16 items per CTA,
- * DYNAMIC otherwise.  Batches use DYNAMIC unless every shot asks for
- * STATIC. */
+ * AUTO: STATIC for an undecomposed shot whose tile columns (the x-y tiles
+ * of one z-chunk) all fit in one round of CTAs, DYNAMIC otherwise.  Batches
+ * use DYNAMIC unless every shot asks for STATIC. */
 enum { GW_SCHED_AUTO = 0, GW_SCHED_STATIC = 1, GW_SCHED_DYNAMIC = 2 };
 
 typedef struct {

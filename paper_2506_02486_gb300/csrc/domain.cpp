@@ -510,11 +510,13 @@ int make_items(const std::vector<SubDev> &subs, const TileInfo &ti, int grid,
         // for the last, uneven round.  At least two chunks per column (one
         // 512-plane item per column: 512^3 1-8 % slower than two), at
         // least 16 planes per item, at most ti.zcap under the dynamic
-        // schedule.  Measured on 512^3 (static): 256-plane items 376
-        // against 353 Gpts/s with 64 for FP32.
+        // schedule and 512 under the static one (the compensated sum of an
+        // item's plane norms then stays within gamma_511^2 = 1e-9).
+        // Measured on 512^3 (static): 256-plane items 376 against 353
+        // Gpts/s with 64 for FP32.
         const bool dyn = dynamic_schedule(sched, (int)subs.size(), ncols, grid);
         const double halo = 8 * 0.7;
-        const int cap = dyn && ti.zcap > 0 ? ti.zcap : std::max(1, nzmax);
+        const int cap = dyn && ti.zcap > 0 ? ti.zcap : 512;
         const int lo = std::max(nzmax >= 32 ? 2 : 1, (nzmax + cap - 1) / cap);
         const int hi = std::max(lo, nzmax / 16);
         double best = 1e300;

@@ -75,9 +75,9 @@ def test_decomposed_equals_undecomposed(reference, px, py, pz, symmetric,
     assert np.array_equal(g["u32"], base["u32"])
     assert np.array_equal(g["traces"], base["traces"])
     # norms: per-thread, per-plane FP32 partials of at most 8 positive
-    # terms, accumulated over an item's <= 128 planes with compensation and
-    # over items in FP64, grouped by tile: each run within gamma_7 +
-    # gamma_127^2 of the exact sum, so the two within twice that
+    # terms, accumulated over an item's planes (fewer than 128 here) with
+    # compensation and over items in FP64, grouped by tile: each run within
+    # gamma_7 + gamma_127^2 of the exact sum, so the two within twice that
     assert g["norms"] == pytest.approx(base["norms"],
                                        rel=2 * (gamma(7) + gamma(127) ** 2))
 

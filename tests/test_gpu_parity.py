@@ -321,9 +321,10 @@ def test_step_norms_are_fp64_sums_of_plane_partials(dtype, u_store):
     """The step kernel's per-step norm, against gw_check's FP64 sum of the
     same field.  Each thread sums its at most 8 points of a plane in the
     math type (positive terms: relative error <= gamma_7 = 7 u / (1 - 7 u)
-    for FP32), accumulates the plane sums of an item (<= 128 planes) as a
-    compensated pair (Ogita, Rump and Oishi's Sum2: error <= gamma_127^2 of
-    the sum), and the items are added in FP64; so for FP32 storage the two
+    for FP32), accumulates the plane sums of an item (fewer than 128 planes
+    on this grid) as a compensated pair (Ogita, Rump and Oishi's Sum2:
+    error <= gamma_127^2 of the sum), and the items are added in FP64; so
+    for FP32 storage the two
     agree to gamma_7 + gamma_127^2, 4.2e-7.  (A plain FP32 partial over an
     item of 64 planes would only be bound by gamma_511 = 3e-5.)  With 16-bit
     storage the kernel squares the values before they are rounded to the
