@@ -370,6 +370,15 @@ gw_status gw_set_model_layered(gw_domain *d, const double *vz);
  * computed in FP64 and rounded to FP32.  Pure host function. */
 gw_status gw_ricker(double f_peak, double dt, int n, float *out);
 
+/* out_dev[i] = in_dev[i] rounded to FP32 (IEEE 754 round to nearest, ties
+ * to even) on the GPU by the integer-arithmetic conversion that the FP32
+ * coefficient precompute (gw_set_model_f32 into FP32 storage) uses, so that
+ * a caller or a test can check it value by value.  in_dev, out_dev: n
+ * elements of device memory owned by the caller.  Enqueued on `stream`,
+ * no host sync; GW_ERR_ARG for NULL arrays with n > 0. */
+gw_status gw_round_to_f32(const double *in_dev, float *out_dev, size_t n,
+                          gw_stream stream);
+
 /* Add a point source at global interior cell (gx, gy, gz) with wavelet
  * samples wavelet[0..n) (FP32 host; sample n is added to lap(u_n) when
  * computing u_{n+1}; steps beyond n add nothing).  Up to 16 sources.

@@ -35,22 +35,26 @@ __device__ __forceinline__ size_t pidx(const SubDev &s, int xo, int x, int y, in
 
 // ---------------------------------------------------------------- vmax
 
+// Max over a dense slab, compared in the input's own type (the max of FP32
+// values is one of them, so comparing FP32 values in FP32 gives the same
+// result as comparing them in FP64, at FP32 speed).
 template <class V>
 __global__ void k_vmax(const V *v, size_t n, unsigned long long *out)
 {
-    double m = 0.0;
+    V m = V(0);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
-        double x = (double)v[i];
+        const V x = v[i];
         m = x > m ? x : m;     // a NaN never wins
     }
+    double md = (double)m;
     for (int o = 16; o > 0; o >>= 1) {
-        double t = __shfl_xor_sync(0xffffffffu, m, o);
-        m = t > m ? t : m;
+        double t = __shfl_xor_sync(0xffffffffu, md, o);
+        md = t > md ? t : md;
     }
     // non-negative doubles order like their bit patterns
-    if ((threadIdx.x & 31) == 0 && m > 0.0)
-        atomicMax(out, (unsigned long long)__double_as_longlong(m));
+    if ((threadIdx.x & 31) == 0 && md > 0.0)
+        atomicMax(out, (unsigned long long)__double_as_longlong(md));
 }
 
 cudaError_t launch_vmax(const void *v, size_t n, int f32,
@@ -68,44 +72,116 @@ cudaError_t launch_vmax(const void *v, size_t n, int f32,
 
 // ---------------------------------------------------------------- coef
 
+// Exact FP32 -> FP64 and round-to-nearest-even FP64 -> FP32 conversions in
+// integer arithmetic, for normal numbers (IEEE 754 binary32 / binary64:
+// rebias the exponent, move the significand; for the narrowing, round the
+// 29 dropped significand bits half to even, carrying into the exponent).
+// Anything else -- zero, subnormal, infinite, NaN, out of FP32's normal
+// range -- takes the hardware conversion.  GB300's FP64 pipe is narrow and
+// conversions to and from FP64 run on it, so the coefficient square below
+// spends it on its two products only.
+__device__ __forceinline__ double f32_to_f64(float v)
+{
+    const uint32_t u = __float_as_uint(v);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)v;
+    const uint64_t b = ((uint64_t)(u >> 31) << 63) | ((uint64_t)(e - 127u + 1023u) << 52) |
+                       ((uint64_t)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ float f64_to_f32_rn(double x)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const int fe = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
+    if (fe <= 0 || fe >= 0xff) return (float)x;
+    const uint64_t m = b & ((1ull << 52) - 1ull);
+    uint32_t r = (uint32_t)(m >> 29);
+    const uint64_t rest = m & ((1ull << 29) - 1ull), half = 1ull << 28;
+    uint32_t ex = (uint32_t)fe;
+    if (rest > half || (rest == half && (r & 1u))) {
+        if (++r == (1u << 23)) {
+            r = 0u;
+            if (++ex == 0xffu) return (float)x;     // rounds to infinity
+        }
+    }
+    return __uint_as_float((uint32_t)(b >> 63) << 31 | ex << 23 | r);
+}
+
+// coef of one input value: (v dt/h)^2 formed in FP64 and rounded to the
+// coef type, or (raw) v itself
+template <class CT, class V> struct CoefOf {
+    __device__ __forceinline__ static CT get(V v, double dt_over_h, int raw)
+    {
+        const double nu = (double)v * dt_over_h;   // FP64 precompute
+        return from_d<CT>(raw ? (double)v : nu * nu);
+    }
+};
+template <> struct CoefOf<float, float> {
+    __device__ __forceinline__ static float get(float v, double dt_over_h, int raw)
+    {
+        if (raw) return v;
+        const double nu = f32_to_f64(v) * dt_over_h;
+        return f64_to_f32_rn(nu * nu);
+    }
+};
+
+// the narrowing conversion above over a device array (the library's
+// conversion pinned against IEEE round-to-nearest-even by the tests)
+__global__ void k_round_to_f32(const double *in, float *out, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = f64_to_f32_rn(in[i]);
+}
+
+cudaError_t launch_round_to_f32(const double *in, float *out, size_t n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int g = (int)std::min<size_t>((n + 255) / 256, 4096);
+    k_round_to_f32<<<g, 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+// One block per row (y, z) of the slab's planes inside the subdomain at a
+// time, threads along x: no per-element index division.
 template <class CT, class V>
 __global__ void k_coef(ModelSlab m, SubDev sd, int xo)
 {
     // planes of the slab inside this subdomain
-    int zl = max(m.z_lo, sd.gz0), zh = min(m.z_hi, sd.gz0 + sd.nz);
+    const int zl = max(m.z_lo, sd.gz0), zh = min(m.z_hi, sd.gz0 + sd.nz);
     if (zl >= zh) return;
-    size_t npl = (size_t)sd.nx * sd.ny;
-    size_t n = npl * (size_t)(zh - zl);
+    const unsigned ny = (unsigned)sd.ny, rows = ny * (unsigned)(zh - zl);
     const V *v = static_cast<const V *>(m.v);
     CT *c = reinterpret_cast<CT *>(sd.coef);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        int x = (int)(i % sd.nx);
-        int y = (int)((i / sd.nx) % sd.ny);
-        int gz = zl + (int)(i / npl);
-        size_t src = m.layered ? (size_t)(gz - m.z_lo)
-                               : ((size_t)(gz - m.z_lo) * m.NY + (size_t)(sd.gy0 + y)) * m.NX +
-                                     (size_t)(sd.gx0 + x);
-        double nu = (double)v[src] * m.dt_over_h;   // FP64 precompute
-        c[pidx(sd, xo, x, y, gz - sd.gz0)] = from_d<CT>(m.raw ? (double)v[src] : nu * nu);
+    for (unsigned r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int y = (int)(r % ny), gz = zl + (int)(r / ny);
+        CT *row = c + pidx(sd, xo, 0, y, gz - sd.gz0);
+        if (m.layered) {
+            const CT cv = CoefOf<CT, V>::get(v[gz - m.z_lo], m.dt_over_h, m.raw);
+            for (int x = threadIdx.x; x < sd.nx; x += blockDim.x) row[x] = cv;
+        } else {
+            const V *src = v + ((size_t)(gz - m.z_lo) * m.NY + (size_t)(sd.gy0 + y)) * m.NX +
+                           (size_t)sd.gx0;
+            for (int x = threadIdx.x; x < sd.nx; x += blockDim.x)
+                row[x] = CoefOf<CT, V>::get(src[x], m.dt_over_h, m.raw);
+        }
     }
 }
 
 // coef = (v dt / h)^2 over a subdomain whose coef array holds v (exactly:
-// only used when the coef type holds the input velocities without rounding)
+// only used when the coef type holds the input velocities without
+// rounding): the same FP64 products, so the same bits as k_coef from the
+// input
 template <class CT>
 __global__ void k_coef_square(SubDev sd, int xo, double dt_over_h)
 {
     CT *c = reinterpret_cast<CT *>(sd.coef);
-    const size_t npl = (size_t)sd.nx * sd.ny, n = npl * (size_t)sd.nz;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % sd.nx);
-        const int y = (int)((i / sd.nx) % sd.ny);
-        const int z = (int)(i / npl);
-        CT &e = c[pidx(sd, xo, x, y, z)];
-        const double nu = to_d<CT>(e) * dt_over_h;   // FP64 precompute
-        e = from_d<CT>(nu * nu);
+    const unsigned ny = (unsigned)sd.ny, rows = ny * (unsigned)sd.nz;
+    for (unsigned r = blockIdx.x; r < rows; r += gridDim.x) {
+        CT *row = c + pidx(sd, xo, 0, (int)(r % ny), (int)(r / ny));
+        for (int x = threadIdx.x; x < sd.nx; x += blockDim.x)
+            row[x] = CoefOf<CT, CT>::get(row[x], dt_over_h, 0);
     }
 }
 
@@ -115,10 +191,18 @@ static int grid_for(size_t n)
     return (int)(g > 8192 ? 8192 : (g ? g : 1));
 }
 
+// blocks for a row walk: one row per block at a time, at most 8 blocks per
+// SM's worth (152 SMs)
+static int grid_rows(size_t rows)
+{
+    return (int)std::min<size_t>(std::max<size_t>(rows, 1), 152 * 8);
+}
+
 cudaError_t launch_coef_square(const SubDev &sd, int dtype, double dt_over_h,
                                cudaStream_t s)
 {
-    const int g = grid_for((size_t)sd.nx * sd.ny * (size_t)sd.nz);
+    if ((size_t)sd.ny * sd.nz > 0xffffffffull) return cudaErrorInvalidValue;
+    const int g = grid_rows((size_t)sd.ny * sd.nz);
     const int xo = dtype_xoff(dtype);
     switch (dtype) {
     case DT_F32: k_coef_square<float><<<g, 256, 0, s>>>(sd, xo, dt_over_h); break;
@@ -131,9 +215,9 @@ cudaError_t launch_coef_square(const SubDev &sd, int dtype, double dt_over_h,
 cudaError_t launch_coef(const ModelSlab &m, const SubDev &sd, int dtype,
                         cudaStream_t s)
 {
-    size_t n = (size_t)sd.nx * sd.ny * (size_t)(m.z_hi - m.z_lo);
-    int g = grid_for(n);
-    int xo = dtype_xoff(dtype);
+    if ((size_t)sd.ny * (size_t)(m.z_hi - m.z_lo) > 0xffffffffull) return cudaErrorInvalidValue;
+    const int g = grid_rows((size_t)sd.ny * (size_t)(m.z_hi - m.z_lo));
+    const int xo = dtype_xoff(dtype);
 #define GW_COEF(CT)                                                     \
     (m.f32 ? (k_coef<CT, float><<<g, 256, 0, s>>>(m, sd, xo), 0)        \
            : (k_coef<CT, double><<<g, 256, 0, s>>>(m, sd, xo), 0))

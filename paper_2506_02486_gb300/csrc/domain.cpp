@@ -947,6 +947,13 @@ gw_status gw_ricker(double f, double dt, int n, float *out)
     return GW_OK;
 }
 
+gw_status gw_round_to_f32(const double *in_dev, float *out_dev, size_t n, gw_stream stream)
+{
+    if (n && (!in_dev || !out_dev)) return fail(GW_ERR_ARG, "NULL array");
+    GW_TRY_CUDA(launch_round_to_f32(in_dev, out_dev, n, static_cast<cudaStream_t>(stream)));
+    return GW_OK;
+}
+
 // Power-of-two scales of FP16 delta storage: keep the largest expected
 // |u| near 2^12 (16x headroom below the FP16 maximum) and w four times
 // larger (w ~ u * omega * dt is smaller than u).

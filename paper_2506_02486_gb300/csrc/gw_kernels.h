@@ -58,6 +58,9 @@ struct ModelSlab {
 };
 cudaError_t launch_coef(const ModelSlab &m, const SubDev &sub, int dtype,
                         cudaStream_t s);
+// out[i] = in[i] rounded to FP32 (nearest, ties to even) by the integer
+// conversion the FP32 coefficient precompute uses.
+cudaError_t launch_round_to_f32(const double *in, float *out, size_t n, cudaStream_t s);
 // In place over a subdomain whose coef array holds velocities (stored by a
 // raw launch_coef): coef = (v dt / h)^2 in FP64, rounded to the coef type.
 cudaError_t launch_coef_square(const SubDev &sub, int dtype, double dt_over_h,

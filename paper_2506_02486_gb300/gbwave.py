@@ -166,6 +166,7 @@ _SIGS = {
     "gw_set_model_f32": [_P, _P],
     "gw_set_model_layered": [_P, _P],
     "gw_ricker": [_D, _D, _I, _P],
+    "gw_round_to_f32": [_P, _P, _SZ, _P],
     "gw_inject_source": [_P, _I, _I, _I, _P, _I],
     "gw_inject_ricker": [_P, _I, _I, _I, _D],
     "gw_set_receivers": [_P, _I, _P],
@@ -541,6 +542,11 @@ def gw_ricker(f_peak: float, dt: float, n: int) -> np.ndarray:
     _check(lib().gw_ricker(float(f_peak), float(dt), int(n), _ptr(out)),
            "gw_ricker")
     return out
+
+
+def gw_round_to_f32(in_dev, out_dev, n: int, stream=None):
+    _check(lib().gw_round_to_f32(_ptr(in_dev), _ptr(out_dev), int(n),
+                                 _stream(stream)), "gw_round_to_f32")
 
 
 def gw_inject_source(dom: int, gx: int, gy: int, gz: int, wavelet):
