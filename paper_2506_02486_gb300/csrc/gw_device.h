@@ -7,7 +7,7 @@
 // with R = 4 halo cells in y and z, a halo of xoff >= R cells in x chosen
 // so that the interior x origin is 32-byte (sector) aligned (xoff = 8 for
 // FP32, 4 for FP64, 16 for 16-bit storage), py = ny + 2R rows per plane and
-// the row pitch px a multiple of 128 bytes.  The array holds nz + 2R planes.
+// the row pitch px a multiple of 32 bytes.  The array holds nz + 2R planes.
 // Halo cells of a subdomain are written only by halo puts (or stay zero at
 // a non-periodic global boundary); padding beyond x = nx + R is never
 // written and stays zero.

@@ -41,10 +41,10 @@ class Segment:
 
 
 def padded_bytes(nx: int, ny: int, nz: int, dtype: str = "f32") -> int:
-    """Bytes of one padded field array (x pitch a multiple of 128 bytes)."""
+    """Bytes of one padded field array (x pitch a multiple of 32 bytes)."""
     es = {"f32": 4, "f64": 8, "f16s": 2, "bf16": 2}[dtype]
     xo = {2: 16, 4: 8, 8: 4}[es]
-    mul = 128 // es
+    mul = 32 // es
     px = -(-(xo + nx + 4) // mul) * mul
     return px * (ny + 8) * (nz + 8) * es
 

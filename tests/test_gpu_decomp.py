@@ -123,7 +123,8 @@ def read_padded(host, base, shot, rank, snx, sny, snz, symmetric, sx, sz):
     # (symmetric: offset 0 on every rank; asymmetric: top of each rank)
     lx = max(sx) if symmetric else snx
     ly = sny
-    px = -(-(8 + lx + 4) // 32) * 32      # FP32: interior at x offset 8
+    px = -(-(8 + lx + 4) // 8) * 8        # FP32: interior at x offset 8,
+                                          # rows a multiple of 32 bytes
     py = ly + 8
     pzp = (max(sz) if symmetric else snz) + 8
     nbytes = px * py * pzp * 4
