@@ -89,7 +89,8 @@ gw_status build_group(gw_batch *b, Group &g)
         int share = (int)std::max<long long>(1, (long long)G * dp / std::max(1LL, pts));
         std::vector<Item> it;
         make_items(d->subs, g.ti, share, d->desc.zchunk,
-                   g.dynamic ? GW_SCHED_DYNAMIC : GW_SCHED_STATIC, it, base);
+                   g.dynamic ? GW_SCHED_DYNAMIC : GW_SCHED_STATIC, it, base,
+                   !b->persistent && b->groups.size() > 1);
         ShotDev sh = d->shot;
         sh.first_item = (int)g.items.size();
         sh.nitems = (int)it.size();

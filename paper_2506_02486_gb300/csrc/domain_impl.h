@@ -19,10 +19,13 @@ long long tile_columns(const std::vector<SubDev> &subs, const TileInfo &ti);
 bool dynamic_schedule(int sched, int nsub, long long ncols, int grid);
 // Work items of `subs` (subdomain indices offset by sub_base) for a tile of
 // ti.tx x ti.ty, z-chunk-major; zchunk <= 0 lets the cost model pick the
-// planes per item for `grid` CTAs under the schedule `sched` would give.
-// Returns the planes per item used.
+// planes per item for `grid` CTAs under the schedule `sched` would give
+// (tail_hidden: other launches run beside this one and fill its last
+// round, so the items only need to be long).  Returns the planes per item
+// used.
 int make_items(const std::vector<SubDev> &subs, const TileInfo &ti, int grid,
-               int zchunk, int sched, std::vector<Item> &items, int sub_base = 0);
+               int zchunk, int sched, std::vector<Item> &items, int sub_base = 0,
+               bool tail_hidden = false);
 }  // namespace gw
 
 using gw::HaloDesc;
