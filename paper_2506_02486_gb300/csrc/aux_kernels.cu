@@ -379,7 +379,9 @@ __global__ void k_chunk_end(const ShotDev *shots, const double *partials,
     const ShotDev &sh = shots[blockIdx.x];
     __shared__ double red[256];
     const int n0 = *sh.step;
-    for (int k = 0; k < nk; ++k) {
+    // steps from the shot's limit on were skipped: no partials, no count
+    const int nk_shot = n0 >= sh.limit ? 0 : min(nk, sh.limit - n0);
+    for (int k = 0; k < nk_shot; ++k) {
         const double *p = partials + (size_t)k * nitems + sh.first_item;
         double v = 0.0;
         for (int i = threadIdx.x; i < sh.nitems; i += blockDim.x) v += p[i];
@@ -396,7 +398,7 @@ __global__ void k_chunk_end(const ShotDev *shots, const double *partials,
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) *sh.step = n0 + nk;
+    if (threadIdx.x == 0) *sh.step = n0 + nk_shot;
 }
 
 cudaError_t launch_chunk_end(const ShotDev *shots_dev, int nshots,

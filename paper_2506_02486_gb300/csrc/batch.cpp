@@ -392,7 +392,8 @@ gw_status gw_batch_step(gw_batch *b, int nsteps, gw_stream stream)
     }
     for (Group &g : b->groups)
         for (gw_domain *d : g.doms) {
-            d->step += nsteps;
+            // a member with a step limit stops there (its launches skip it)
+            d->step = (int)std::min<long long>((long long)d->step + nsteps, d->shot.limit);
             d->last = s;
         }
     return GW_OK;

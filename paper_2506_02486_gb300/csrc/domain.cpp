@@ -6,6 +6,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 
@@ -785,6 +786,7 @@ gw_status gw_domain_create(gw_ctx *c, const gw_shot_desc *desc, int px, int py,
     sh.src = d->d_src;
     sh.rec = nullptr;
     sh.cap = cap;
+    sh.limit = INT_MAX;
     sh.nsrc = 0;
     sh.nrec = 0;
     sh.NX = D.nx; sh.NY = D.ny; sh.NZ = D.nz;
@@ -1119,12 +1121,12 @@ gw_status gw_step(gw_domain *d, int nsteps, gw_stream stream)
             GW_TRY(ensure_graph(d));
             GW_TRY_CUDA(cudaGraphLaunch(d->gexec, s));
             left -= d->chunk;
-            d->step += d->chunk;
+            d->step = std::min(d->step + d->chunk, d->shot.limit);
         } else {
             int nk = std::min(left, d->chunk);
             GW_TRY(enqueue_chunk(d, nk, s, d->timing));
             left -= nk;
-            d->step += nk;
+            d->step = std::min(d->step + nk, d->shot.limit);
         }
     }
     return GW_OK;

@@ -69,6 +69,9 @@ struct ShotDev {
     float isu, isw;        // their inverses
     int lo[2][3], hi[2][3];   // bounding boxes of the sources [0] and of the
                               // receivers [1] (global cells; lo > hi: none)
+    int limit;             // steps the shot takes at most: launches skip its
+                           // items from step `limit` on and its counter
+                           // stops there (INT_MAX: no limit)
 };
 
 // One work item: a tile column (x0, y0) of subdomain `sub`, planes [z0, z1).

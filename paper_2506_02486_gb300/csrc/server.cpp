@@ -113,6 +113,9 @@ gw_status setup(gw_server *S, Req *q)
     if (q->r.nrec) GW_TRY(gw_set_receivers(q->dom, q->r.nrec, q->rec.data()));
     q->res.tile = q->dom->cfg + 1;
     q->left = d.nsteps;
+    // the shot stops at its own step count inside a longer chunk of the
+    // batch (its launches skip it from there on)
+    q->dom->shot.limit = d.nsteps;
     return GW_OK;
 }
 
@@ -218,12 +221,13 @@ void loop(gw_server *S)
             }
             dirty = false;
         }
-        int K = S->chunk;
+        // chunks of K steps for every member; a member with fewer steps
+        // left stops at its limit inside the chunk, so K is set by the
+        // member with the most steps left (at most the server's chunk)
+        int K = 1;
         long long pts = 0;
-        for (Req *q : S->active) {
-            K = std::min(K, q->left);
-            pts += q->points;
-        }
+        for (Req *q : S->active) K = std::max(K, std::min(S->chunk, q->left));
+        for (Req *q : S->active) pts += q->points * std::min(K, q->left);
         const double t_launch = S->now();
         gw_status st = GW_OK;
         // the storage types' batches run side by side, one stream each
@@ -247,7 +251,7 @@ void loop(gw_server *S)
         {
             std::lock_guard<std::mutex> lk(S->mu);
             S->st.chunks++;
-            S->st.point_updates += pts * K;
+            S->st.point_updates += pts;
             S->st.busy_s += S->now() - t_launch;
         }
         std::vector<Req *> keep;

@@ -489,14 +489,22 @@ struct Step {
         }
         for (;;) {
             const int it = claim_item(nth);
+            Item I{};
+            int n = 0;
+            if (it >= 0) {
+                I = A.items[it];
+                const ShotDev &sh0 = A.shots[A.subs[I.sub].shot];
+                n = *sh0.step + A.k + k;
+                // a shot that has taken all its steps (a batch member that
+                // finishes inside the chunk) is left as it is
+                if (n >= sh0.limit) continue;
+            }
             if (!publish_item(it, iqn)) {
                 *abortf() = 1;
                 goto drain;
             }
             if (it < 0) break;
-            const Item I = A.items[it];
-            const SubDev &s = A.subs[I.sub];
-            const int p = (*A.shots[s.shot].step + A.k + k) & 1;
+            const int p = n & 1;
             const char *base = static_cast<const char *>(A.maps) +
                                (size_t)I.sub * kMapsPerSub * 128;
             const char *map_u = base + (p ? MAP_U1_HALO : MAP_U0_HALO) * 128;
