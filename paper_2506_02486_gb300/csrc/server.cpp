@@ -6,6 +6,7 @@
 // groups side by side within it), and retires shots
 // at chunk boundaries (traces to the caller's buffer, final check).
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -41,6 +42,7 @@ struct gw_server {
     int slots = 0;
     int chunk = kDefaultChunk;
     cudaStream_t streams[4] = {nullptr, nullptr, nullptr, nullptr};  // one per storage type
+    cudaStream_t aux = nullptr;  // reading finished shots while a chunk runs
     Clock::time_point t0;
     std::thread th;
 
@@ -58,6 +60,8 @@ struct gw_server {
 
     // loop thread only
     std::vector<Req *> active;
+    std::vector<Req *> retiring;   // finished in the last chunk, not yet read
+    std::vector<std::pair<gw_domain *, size_t>> grave;   // read; freed after the chunk
     gw_batch *batch[4] = {nullptr, nullptr, nullptr, nullptr};
 
     double now() const
@@ -83,21 +87,36 @@ void take_admissible(gw_server *S, std::vector<Req *> &out)
     }
 }
 
-void finish(gw_server *S, Req *q, gw_status status)
+// The result is ready: gw_wait hands it out (and frees q).  The shot's
+// domain and its share of the budget go separately (release), so that a
+// shot can be completed while the next chunk runs and freed once no launch
+// covers it any more.
+void complete(gw_server *S, Req *q, gw_status status)
 {
-    if (q->dom) {
-        gw_domain_destroy(q->dom);
-        q->dom = nullptr;
-    }
     std::lock_guard<std::mutex> lk(S->mu);
     q->res.status = status;
     q->res.done_s = S->now();
-    S->used -= q->bytes;
     S->live.erase(q->ticket);
     S->done[q->ticket] = q;
     S->st.completed++;
-    S->blocked = false;
     S->cv_done.notify_all();
+}
+
+void release(gw_server *S, gw_domain *dom, size_t bytes)
+{
+    if (dom) gw_domain_destroy(dom);
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->used -= bytes;
+    S->blocked = false;
+}
+
+void finish(gw_server *S, Req *q, gw_status status)
+{
+    gw_domain *dom = q->dom;
+    const size_t bytes = q->bytes;
+    q->dom = nullptr;
+    complete(S, q, status);
+    release(S, dom, bytes);
 }
 
 // Create the shot's domain and load its model, source and receivers.
@@ -178,14 +197,60 @@ gw_status rebuild(gw_server *S)
     return GW_OK;
 }
 
-void retire(gw_server *S, Req *q)
+// A finished shot's traces and final check (the sums of gw_check, by the
+// same kernels) on the server's own stream: no launch of the running chunk
+// covers the shot any more, so this waits for nothing else on the device
+// (gw_read_receivers and gw_check would wait for the whole device).
+gw_status collect(gw_server *S, Req *q)
 {
-    gw_status st = GW_OK;
+    gw_domain *d = q->dom;
+    cudaStream_t s = S->aux;
+    unsigned err = 0;
+    double a[3] = {0.0, 0.0, 0.0};
+    GW_TRY_CUDA(cudaMemcpyAsync(&err, d->d_err, sizeof err, cudaMemcpyDeviceToHost, s));
     const int n = q->r.desc.nsteps;
     if (q->r.traces && q->r.nrec)
-        st = gw_read_receivers(q->dom, q->r.traces, q->r.nrec, n);
-    if (st == GW_OK) st = gw_check(q->dom, &q->res.norm2, &q->res.energy);
-    finish(S, q, st);
+        GW_TRY_CUDA(cudaMemcpy2DAsync(q->r.traces, sizeof(float) * n, d->d_traces,
+                                      sizeof(float) * d->shot.cap, sizeof(float) * n,
+                                      q->r.nrec, cudaMemcpyDeviceToHost, s));
+    int planes = 0;
+    for (const SubDev &sd : d->subs) {
+        GW_TRY_CUDA(launch_check(sd, d->step & 1, d->dtype, d->su, d->d_chk + 3 * planes, s));
+        planes += sd.nz;
+    }
+    GW_TRY_CUDA(launch_check_sum(d->d_chk, planes, d->d_scratch, s));
+    GW_TRY_CUDA(cudaMemcpyAsync(a, d->d_scratch, sizeof a, cudaMemcpyDeviceToHost, s));
+    GW_TRY_CUDA(cudaStreamSynchronize(s));
+    if (err & ERRB_TIMEOUT) return fail(GW_ERR_TIMEOUT, "a device wait gave up (error bits 0x%x)", err);
+    if (err & ERRB_NONFINITE) return fail(GW_ERR_NUMERIC, "non-finite wavefield norm (error bits 0x%x)", err);
+    if (err) return fail(GW_ERR_STATE, "device error bits 0x%x", err);
+    q->res.norm2 = a[0];
+    q->res.energy = a[1] - a[2];
+    if (!std::isfinite(a[0]) || !std::isfinite(a[1]) || !std::isfinite(a[2]))
+        return fail(GW_ERR_NUMERIC, "non-finite check reduction");
+    return GW_OK;
+}
+
+// Complete the shots that finished in the last chunk; their domains go to
+// the grave (freed after the next chunk) or, with nothing running, at once.
+void retire_all(gw_server *S, bool now)
+{
+    for (Req *q : S->retiring) {
+        const gw_status st = collect(S, q);
+        gw_domain *dom = q->dom;
+        const size_t bytes = q->bytes;
+        q->dom = nullptr;
+        complete(S, q, st);
+        if (now) release(S, dom, bytes);
+        else S->grave.push_back({dom, bytes});
+    }
+    S->retiring.clear();
+}
+
+void free_grave(gw_server *S)
+{
+    for (auto &g : S->grave) release(S, g.first, g.second);
+    S->grave.clear();
 }
 
 void loop(gw_server *S)
@@ -196,7 +261,7 @@ void loop(gw_server *S)
         std::vector<Req *> adm;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            if (S->active.empty()) {
+            if (S->active.empty() && S->retiring.empty()) {
                 S->cv_work.wait(lk, [&] {
                     return S->stop || (!S->pending.empty() && !S->blocked);
                 });
@@ -211,7 +276,11 @@ void loop(gw_server *S)
                 dirty = true;
             }
         }
-        if (S->active.empty()) continue;
+        if (S->active.empty()) {
+            // nothing to run beside it: finish the last shots now
+            retire_all(S, true);
+            continue;
+        }
         if (dirty) {
             gw_status st = rebuild(S);
             if (st != GW_OK) {
@@ -233,7 +302,9 @@ void loop(gw_server *S)
         // the storage types' batches run side by side, one stream each
         for (int t = 0; t < 4; ++t)
             if (S->batch[t] && st == GW_OK) st = gw_batch_step(S->batch[t], K, S->streams[t]);
-        // while the chunk runs: admit and set up the next shots
+        // while the chunk runs: complete the shots of the last chunk, admit
+        // and set up the next ones
+        retire_all(S, false);
         std::vector<Req *> joiners;
         if (st == GW_OK) {
             {
@@ -254,6 +325,8 @@ void loop(gw_server *S)
             S->st.point_updates += pts;
             S->st.busy_s += S->now() - t_launch;
         }
+        // no launch covers the shots completed during this chunk any more
+        free_grave(S);
         std::vector<Req *> keep;
         for (Req *q : S->active) {
             if (st != GW_OK) {
@@ -265,7 +338,8 @@ void loop(gw_server *S)
             if (q->left > 0) {
                 keep.push_back(q);
             } else {
-                retire(S, q);
+                // read during the next chunk (or at once if none runs)
+                S->retiring.push_back(q);
                 dirty = true;
             }
         }
@@ -279,6 +353,8 @@ void loop(gw_server *S)
     }
     // stopped: nothing runs any more
     for (cudaStream_t x : S->streams) cudaStreamSynchronize(x);
+    free_grave(S);
+    retire_all(S, true);
     for (gw_batch *&b : S->batch) {
         if (b) gw_batch_destroy(b);
         b = nullptr;
@@ -319,7 +395,10 @@ gw_status gw_server_create(gw_ctx *c, size_t hbm_budget, int max_slots, int chun
     cudaError_t e = cudaSetDevice(c->device);
     for (int t = 0; t < 4 && e == cudaSuccess; ++t)
         e = cudaStreamCreateWithFlags(&S->streams[t], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->aux, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
+        for (cudaStream_t x : S->streams)
+            if (x) cudaStreamDestroy(x);
         delete S;
         return cuda_fail(e, "cudaStreamCreateWithFlags");
     }
@@ -329,6 +408,7 @@ gw_status gw_server_create(gw_ctx *c, size_t hbm_budget, int max_slots, int chun
     } catch (...) {
         for (cudaStream_t x : S->streams)
             if (x) cudaStreamDestroy(x);
+        cudaStreamDestroy(S->aux);
         delete S;
         return fail(GW_ERR_NOMEM, "cannot start the server thread");
     }
@@ -348,6 +428,7 @@ gw_status gw_server_destroy(gw_server *S)
     for (auto &kv : S->done) delete kv.second;
     for (cudaStream_t x : S->streams)
         if (x) cudaStreamDestroy(x);
+    if (S->aux) cudaStreamDestroy(S->aux);
     delete S;
     return GW_OK;
 }
