@@ -506,11 +506,15 @@ gw_status gw_autotune(gw_ctx *ctx, const gw_shot_desc *desc, int px, int py,
                       int pz, int steps, int *best_tile, double *best_ms,
                       double *ms_all, int n_all);
 /* Tiles for a batch of n single-domain shots of one storage type: each
- * distinct shape is autotuned (as gw_autotune, cached), then one tile for
- * every shot is chosen (the one with the least summed time) unless the
- * per-shape best tiles are faster in sum by more than `margin` (e.g. 0.05):
- * shots with different tiles launch one group after the other, which the
- * per-shape timings do not see.  tiles_out[i] receives shot i's tile. */
+ * distinct shape is autotuned at full occupancy (as gw_autotune, cached, on
+ * the shot's x-y plane over enough planes for 64 M points, times scaled
+ * back to the shot's planes: a small shot alone would time one CTA's
+ * latency rather than the tile's throughput inside a batch; the shot's own
+ * shape when the segment has no room for that), then one tile
+ * for every shot is chosen (the one with the least summed time) unless the
+ * per-shape best tiles are faster in sum by more than `margin` (e.g. 0.05;
+ * 0 when the tile groups run side by side, as a non-persistent batch's
+ * do).  tiles_out[i] receives shot i's tile. */
 gw_status gw_plan_tiles(gw_ctx *ctx, int n, const gw_shot_desc *descs, int steps,
                         double margin, int *tiles_out);
 /* Tile model (host only, no timing): the tile expected to move the fewest

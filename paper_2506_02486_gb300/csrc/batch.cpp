@@ -472,8 +472,8 @@ extern "C" gw_status gw_autotune(gw_ctx *c, const gw_shot_desc *desc, int px, in
         dd.nsteps = warm + steps;
         dd.persistent = 0;
         dd.dt = 0;
-        const size_t npts = (size_t)desc->nx * desc->ny * desc->nz;
-        std::vector<float> vel(npts, 2000.0f);
+        // a constant model, set per plane (no host array of the whole grid)
+        const std::vector<double> vz((size_t)desc->nz, 2000.0);
         std::vector<double> times(ncfg, 0.0);
         for (int t = 1; t <= ncfg; ++t) {
             dd.tile = t;
@@ -486,7 +486,7 @@ extern "C" gw_status gw_autotune(gw_ctx *c, const gw_shot_desc *desc, int px, in
                 return st;
             }
             gw_kernel_stats ks{};
-            st = gw_set_model_f32(d, vel.data());
+            st = gw_set_model_layered(d, vz.data());
             if (st == GW_OK) st = gw_step(d, warm, nullptr);
             if (st == GW_OK) st = gw_kernel_timing(d, 1);
             if (st == GW_OK) st = gw_step(d, steps, nullptr);
@@ -521,9 +521,27 @@ extern "C" gw_status gw_plan_tiles(gw_ctx *c, int n, const gw_shot_desc *descs, 
     double mixed = 0;
     for (int i = 0; i < n; ++i) {
         if (descs[i].dtype != dtype) return fail(GW_ERR_ARG, "shots must share one storage type");
+        // time each tile at full occupancy: the shot's x-y plane over enough
+        // planes for 64 M points.  A small shot alone keeps few CTAs busy
+        // and times the latency of one CTA's items, not what the tile
+        // delivers inside a batch that fills the GPU.  Per point, scaled
+        // back to the shot's own planes.
+        gw_shot_desc td = descs[i];
+        const long long plane = (long long)td.nx * td.ny;
+        const long long want = (64LL << 20) / std::max(1LL, plane);
+        td.nz = (int)std::max<long long>(td.nz, std::min<long long>(want, 4096));
         int best = 0;
         double bms = 0;
-        GW_TRY(gw_autotune(c, &descs[i], 1, 1, 1, steps, &best, &bms, times.data(), ncfg));
+        gw_status st = gw_autotune(c, &td, 1, 1, 1, steps, &best, &bms, times.data(), ncfg);
+        if (st == GW_ERR_BUDGET && td.nz != descs[i].nz) {
+            // no room in the segment for the taller scratch shot: its own shape
+            td = descs[i];
+            st = gw_autotune(c, &td, 1, 1, 1, steps, &best, &bms, times.data(), ncfg);
+        }
+        GW_TRY(st);
+        const double scale = (double)descs[i].nz / td.nz;
+        for (double &t : times) t *= scale;
+        bms *= scale;
         tiles_out[i] = best;
         mixed += bms;
         for (int t = 0; t < ncfg; ++t) {
