@@ -251,7 +251,7 @@ def bench_config(shot) -> dict:
             "model": "8 layers, velocities U[1500, 4500] m/s, seed 2506",
             "sponge": shot.sponge, "source_hz": shot.f_peak,
             "receivers": int(shot.receivers.shape[0]),
-            "l2": "inputs larger than L2: 3 fields x 588 MB streamed per step"}
+            "l2": "inputs larger than L2: 3 fields x 571 MB streamed per step"}
 
 
 def run_reference(args, world, rank, pg):
